@@ -1,0 +1,231 @@
+/*
+ * catfhe: the RNS hot path of CKKS / BFV / BGV homomorphic multiplication
+ * with relinearisation, rotation and rescale / modulus switching, as
+ * hand-written CUDA for GB300 (sm_103a), behind a plain C ABI.
+ *
+ * Paper: Q. Li, R. Zong, "CAT: A GPU-Accelerated FHE Framework with Its
+ * Application to High-Precision Private Dataset Query" (arXiv 2503.22227).
+ * The operations are the upper-layer operators of its Sec. 3 (key
+ * generation, encrypt / decrypt, add, multiply, relinearize, rescale,
+ * rotate; Tables 1-3), over the RNS representation of its Sec. 2.2.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Return value: CATFHE_OK (0) on success, else a negative CATFHE_E* code;
+ *   catfhe_strerror() names it.  On error nothing is written to outputs.
+ * Handles: catfhe_ctx and catfhe_keys are created and owned by the library
+ *   and freed by their _destroy call.  They hold device memory (prime and
+ *   NTT tables, keys) allocated once with cudaMalloc on the current device.
+ * Ciphertexts: plain device pointers to uint64 residues, "limb-major"
+ *   (Sec. 3.1.5 of the paper: the residues of one modulus are contiguous,
+ *   one modulus after another).  A batch of `count` ciphertexts at level l
+ *   (primes q_0 .. q_{l-1}) is  u64[count][2][l][N],  every residue in
+ *   [0, q_i).  At rest, CKKS and BGV ciphertexts are in NTT (evaluation)
+ *   form and BFV ciphertexts in coefficient form; the NTT order is
+ *   internal.  catfhe_ct_export gives the coefficient form.
+ *   Device buffers are caller-owned; the library only reads inputs and
+ *   writes outputs during the stream-ordered work it enqueues.  `out` may
+ *   alias an input of the same shape.
+ * Workspace: operations that need scratch take (ws, ws_bytes): a device
+ *   buffer of at least catfhe_workspace_bytes(...) bytes, 256-byte aligned,
+ *   caller-owned, not touched after the enqueued work completes.  ws = NULL
+ *   makes the library use a scratch buffer owned by the context (grown
+ *   with cudaMalloc on demand; calls that share it must be ordered on one
+ *   stream).
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  All
+ *   device work is enqueued on it and is asynchronous, except where a
+ *   function says it synchronises (those that write host memory).
+ * Seeds: 32 bytes.  All randomness is ChaCha20 (RFC 8439) keyed by the
+ *   seed, so keys and encryptions are reproducible bit for bit.
+ */
+#ifndef CATFHE_H
+#define CATFHE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CATFHE_OK = 0,
+    CATFHE_EINVAL = -1,     /* bad argument, shape or parameter set          */
+    CATFHE_ELEVEL = -2,     /* level out of range, or rescale at level 1     */
+    CATFHE_ENOKEY = -3,     /* the key-switching key is missing              */
+    CATFHE_ENOMEM = -4,     /* device allocation failed                      */
+    CATFHE_ECUDA = -5,      /* a CUDA call or kernel launch failed           */
+    CATFHE_ESCHEME = -6,    /* operation not defined for this scheme         */
+    CATFHE_EWORKSPACE = -7  /* workspace smaller than required               */
+};
+
+enum { CATFHE_CKKS = 0, CATFHE_BFV = 1, CATFHE_BGV = 2 };
+
+/* Operation codes for catfhe_workspace_bytes. */
+enum {
+    CATFHE_OP_MUL_RELIN = 1,
+    CATFHE_OP_MUL_RELIN_RESCALE = 2,
+    CATFHE_OP_ROTATE = 3,
+    CATFHE_OP_RESCALE = 4,
+    CATFHE_OP_DECRYPT = 5,
+    CATFHE_OP_EXPORT = 6,
+    CATFHE_OP_NTT = 7
+};
+
+/* Forms for catfhe_ct_import / catfhe_ct_export. */
+enum { CATFHE_FORM_COEFF = 0, CATFHE_FORM_NATIVE = 1 };
+
+/*
+ * Parameter set (paper Sec. 2.2: q = prod q_i of word-sized coprime
+ * moduli; Sec. 5.1 fixes N, L and log Q per experiment).
+ *   scheme     CATFHE_CKKS / _BFV / _BGV
+ *   log_n      ring degree N = 2^log_n, 10 <= log_n <= 16
+ *   log_n_max  every prime is 1 mod 2^(log_n_max+1) (>= log_n; lets one
+ *              chain serve several ring degrees)
+ *   L, q_bits  L ciphertext primes; prime i is the largest unused prime
+ *              below 2^q_bits[i] that is 1 mod 2^(log_n_max+1)
+ *   K, p_bits  K special primes for hybrid key switching (chosen after Q)
+ *   dnum       number of key-switching digits: alpha = ceil(L/dnum)
+ *              primes per digit
+ *   t          plaintext modulus (BFV, BGV; ignored for CKKS), odd,
+ *              coprime to every prime, t < 2^61
+ *   aux_count  BFV auxiliary basis size; 0 = the smallest count with
+ *              prod(B) > 2 t N Q
+ *   aux_bits   BFV auxiliary prime size (0 = 60)
+ * Prime sizes: 20 <= bits <= 61.
+ */
+typedef struct {
+    int32_t scheme;
+    int32_t log_n;
+    int32_t log_n_max;
+    int32_t L;
+    int32_t K;
+    int32_t dnum;
+    int32_t q_bits[64];
+    int32_t p_bits[16];
+    uint64_t t;
+    int32_t aux_count;
+    int32_t aux_bits;
+} catfhe_params;
+
+typedef struct {
+    int32_t n;       /* ring degree                         */
+    int32_t L, K;    /* ciphertext and special prime counts */
+    int32_t nb;      /* BFV auxiliary primes (0 otherwise)  */
+    int32_t alpha;   /* primes per key-switching digit      */
+    int32_t beta;    /* digits at the top level             */
+} catfhe_info;
+
+typedef struct catfhe_ctx catfhe_ctx;
+typedef struct catfhe_keys catfhe_keys;
+
+const char *catfhe_strerror(int code);
+
+/* Creates a context on the current CUDA device: generates the primes,
+ * the NTT tables (smallest primitive 2N-th root of each prime, powers in
+ * bit-reversed order) and the base-conversion constants.  Synchronises. */
+int catfhe_ctx_create(const catfhe_params *params, catfhe_ctx **out);
+void catfhe_ctx_destroy(catfhe_ctx *ctx);
+int catfhe_ctx_info(const catfhe_ctx *ctx, catfhe_info *out);
+/* Copies the primes to host arrays of L, K and nb entries (any may be NULL). */
+int catfhe_ctx_moduli(const catfhe_ctx *ctx, uint64_t *q, uint64_t *p, uint64_t *b);
+
+/* Galois element 5^steps mod 2N (left rotation of CKKS slots / BFV and
+ * BGV rows by `steps`); steps may be negative.  Returns 0 on bad ctx. */
+uint64_t catfhe_galois_elt(const catfhe_ctx *ctx, int64_t steps);
+
+/* Key generation from a seed (paper Sec. 3: "key generation periods of
+ * various types"): ternary secret s, public key (-a s + e, a) (BGV: t e),
+ * and the relinearisation key switching s^2 -> s.  Synchronises. */
+int catfhe_keygen(catfhe_ctx *ctx, const uint8_t seed[32], catfhe_keys **out);
+/* Adds the key switching sigma_g(s) -> s, g odd (rotation / conjugation). */
+int catfhe_gen_galois_key(catfhe_ctx *ctx, catfhe_keys *keys, uint64_t galois_elt);
+void catfhe_keys_destroy(catfhe_keys *keys);
+/* Exports keys in coefficient form to host memory (for checking):
+ * s: int64[N]; pk: u64[2][L][N]; ksk (key_id 0 = relinearisation, else a
+ * Galois element): u64[beta][2][L+K][N].  Any pointer may be NULL.
+ * Synchronises. */
+int catfhe_keys_export(catfhe_ctx *ctx, const catfhe_keys *keys, uint64_t key_id,
+                       int64_t *s, uint64_t *pk, uint64_t *ksk);
+
+/* Public-key encryption of the integer polynomial msg (host, int64[N]) at
+ * the top level L into ct (device, u64[2][L][N]).  CKKS: msg is the
+ * encoded, scaled plaintext; BFV / BGV: msg in [0, t).  Synchronises on
+ * the upload of msg. */
+int catfhe_encrypt(catfhe_ctx *ctx, const catfhe_keys *keys, const int64_t *msg,
+                   const uint8_t seed[32], uint64_t *ct, void *stream);
+
+/* A ciphertext with residues uniform mod q_i (coefficient form, ChaCha20
+ * domain "ct_uniform", indexes poly and `index`), stored at rest. */
+int catfhe_ct_uniform(catfhe_ctx *ctx, const uint8_t seed[32], uint32_t index,
+                      uint32_t level, uint64_t *ct, void *stream);
+
+/* Host <-> device transfer of `count` ciphertexts u64[count][2][level][N].
+ * FORM_COEFF: host data in coefficient form (converted to / from the at-
+ * rest form on the device).  FORM_NATIVE: host data in the at-rest form
+ * (plain copies).  export needs workspace only for FORM_COEFF; it
+ * synchronises `stream`.  import synchronises on the host copy. */
+int catfhe_ct_import(catfhe_ctx *ctx, const uint64_t *host, uint32_t level, uint32_t count,
+                     int form, uint64_t *ct, void *stream);
+int catfhe_ct_export(catfhe_ctx *ctx, const uint64_t *ct, uint32_t level, uint32_t count,
+                     int form, uint64_t *host, void *ws, size_t ws_bytes, void *stream);
+
+/* out = a + b (Table 1-3 "add"), count ciphertexts at `level`. */
+int catfhe_add(catfhe_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out,
+               uint32_t level, uint32_t count, void *stream);
+
+/* Homomorphic multiplication with relinearisation (Tables 1-3 "multiply"
+ * then "relinearize"): tensor (d0, d1, d2) = (a0 b0, a0 b1 + a1 b0, a1 b1)
+ * (BFV: exact round(t x / Q) of the tensor over Q u B), then hybrid key
+ * switching of d2 with the relinearisation key: exact ModUp of each digit
+ * to Q_l u P, inner product with the key, exact ModDown round(x / P)
+ * (BGV: (x - d) / P with d = t [x t^-1]_P).  Output at `level`. */
+int catfhe_mul_relin(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
+                     const uint64_t *b, uint64_t *out, uint32_t level, uint32_t count,
+                     void *ws, size_t ws_bytes, void *stream);
+
+/* CKKS only: multiply, relinearise and rescale in one fused pass; the
+ * ModDown and the rescale are one exact division by P q_{l-1}, equal bit
+ * for bit to catfhe_mul_relin followed by catfhe_rescale.  Output at
+ * level-1, u64[count][2][level-1][N]. */
+int catfhe_mul_relin_rescale(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
+                             const uint64_t *b, uint64_t *out, uint32_t level,
+                             uint32_t count, void *ws, size_t ws_bytes, void *stream);
+
+/* Rotation (Table 1 "rotate_vector_one_step", Tables 2-3 rotate rows /
+ * columns): out = (sigma_g(a0), 0) + KS(sigma_g(a1)) with the Galois key of
+ * g; g = catfhe_galois_elt(steps), or 2N-1 for conjugation / columns. */
+int catfhe_rotate(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
+                  uint64_t galois_elt, uint64_t *out, uint32_t level, uint32_t count,
+                  void *ws, size_t ws_bytes, void *stream);
+
+/* CKKS rescale round(c / q_{l-1}) (Table 1 "rescale"), or BGV modulus
+ * switch (c - d) / q_{l-1}, d = t [c t^-1]_{q_{l-1}} (the plaintext then
+ * carries the factor q_{l-1}^-1 mod t, see catfhe_decrypt).  Output at
+ * level-1.  ESCHEME for BFV, ELEVEL at level 1. */
+int catfhe_rescale(catfhe_ctx *ctx, const uint64_t *a, uint64_t *out, uint32_t level,
+                   uint32_t count, void *ws, size_t ws_bytes, void *stream);
+
+/* Decryption of one ciphertext at `level` into host msg (int64[N]):
+ * x = [c0 + c1 s]_{Q_l} centred; CKKS: x as two's complement (exact when
+ * |x| < 2^63); BFV: round(t x / Q_l) mod t; BGV: x factor^-1 mod t where
+ * `factor` is the plaintext factor accumulated by modulus switches (1 for
+ * a fresh or multiplied ciphertext).  Synchronises. */
+int catfhe_decrypt(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *ct,
+                   uint32_t level, uint64_t factor, int64_t *msg, void *ws, size_t ws_bytes,
+                   void *stream);
+
+/* Batched negacyclic NTT (paper Sec. 3.1.3) in place over count*level
+ * limbs u64[count][level][N], limb i of each group mod q_i.  inverse != 0
+ * runs the inverse transform (N^-1 folded in).  No workspace. */
+int catfhe_ntt(catfhe_ctx *ctx, uint64_t *limbs, uint32_t level, uint32_t count, int inverse,
+               void *stream);
+
+/* Workspace bytes that `op` needs for `count` ciphertexts at `level`. */
+size_t catfhe_workspace_bytes(const catfhe_ctx *ctx, int op, uint32_t level, uint32_t count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CATFHE_H */

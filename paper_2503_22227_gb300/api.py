@@ -1,0 +1,318 @@
+"""Thin Python binding of the C ABI in ``include/catfhe.h``.
+
+Argument marshalling only: every step of every operation runs in the CUDA
+kernels of ``libcatfhe.so``.  PyTorch supplies device memory (ciphertexts
+and workspaces are ``torch.int64`` CUDA tensors holding the uint64
+residues bit for bit) and the current CUDA stream.  There is no CPU
+fallback: if the library is missing, :func:`load` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import workloads as W
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcatfhe.so")
+
+CKKS, BFV, BGV = 0, 1, 2
+OP_MUL_RELIN, OP_MUL_RELIN_RESCALE, OP_ROTATE, OP_RESCALE, OP_DECRYPT, OP_EXPORT, OP_NTT = range(1, 8)
+FORM_COEFF, FORM_NATIVE = 0, 1
+
+# every symbol include/catfhe.h declares
+EXPORTS = [
+    "catfhe_strerror", "catfhe_ctx_create", "catfhe_ctx_destroy", "catfhe_ctx_info",
+    "catfhe_ctx_moduli", "catfhe_galois_elt", "catfhe_keygen", "catfhe_gen_galois_key",
+    "catfhe_keys_destroy", "catfhe_keys_export", "catfhe_encrypt", "catfhe_ct_uniform",
+    "catfhe_ct_import", "catfhe_ct_export", "catfhe_add", "catfhe_mul_relin",
+    "catfhe_mul_relin_rescale", "catfhe_rotate", "catfhe_rescale", "catfhe_decrypt",
+    "catfhe_ntt", "catfhe_workspace_bytes",
+]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int32), ("log_n", ctypes.c_int32),
+                ("log_n_max", ctypes.c_int32), ("L", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("dnum", ctypes.c_int32), ("q_bits", ctypes.c_int32 * 64),
+                ("p_bits", ctypes.c_int32 * 16), ("t", ctypes.c_uint64),
+                ("aux_count", ctypes.c_int32), ("aux_bits", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("L", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("nb", ctypes.c_int32), ("alpha", ctypes.c_int32), ("beta", ctypes.c_int32)]
+
+
+class CatfheError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {_lib.catfhe_strerror(code).decode()} ({code})")
+
+
+_lib = None
+_lock = threading.Lock()
+vp, u64, i64, u32, sz = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_size_t
+u8p = ctypes.POINTER(ctypes.c_uint8)
+
+
+def load(path: str = LIB_PATH):
+    """Loads libcatfhe.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libcatfhe.so not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        sig = {
+            "catfhe_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            "catfhe_ctx_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(vp)]),
+            "catfhe_ctx_destroy": (None, [vp]),
+            "catfhe_ctx_info": (ctypes.c_int, [vp, ctypes.POINTER(Info)]),
+            "catfhe_ctx_moduli": (ctypes.c_int, [vp, vp, vp, vp]),
+            "catfhe_galois_elt": (u64, [vp, i64]),
+            "catfhe_keygen": (ctypes.c_int, [vp, u8p, ctypes.POINTER(vp)]),
+            "catfhe_gen_galois_key": (ctypes.c_int, [vp, vp, u64]),
+            "catfhe_keys_destroy": (None, [vp]),
+            "catfhe_keys_export": (ctypes.c_int, [vp, vp, u64, vp, vp, vp]),
+            "catfhe_encrypt": (ctypes.c_int, [vp, vp, vp, u8p, vp, vp]),
+            "catfhe_ct_uniform": (ctypes.c_int, [vp, u8p, u32, u32, vp, vp]),
+            "catfhe_ct_import": (ctypes.c_int, [vp, vp, u32, u32, ctypes.c_int, vp, vp]),
+            "catfhe_ct_export": (ctypes.c_int, [vp, vp, u32, u32, ctypes.c_int, vp, vp, sz, vp]),
+            "catfhe_add": (ctypes.c_int, [vp, vp, vp, vp, u32, u32, vp]),
+            "catfhe_mul_relin": (ctypes.c_int, [vp, vp, vp, vp, vp, u32, u32, vp, sz, vp]),
+            "catfhe_mul_relin_rescale": (ctypes.c_int, [vp, vp, vp, vp, vp, u32, u32, vp, sz, vp]),
+            "catfhe_rotate": (ctypes.c_int, [vp, vp, vp, u64, vp, u32, u32, vp, sz, vp]),
+            "catfhe_rescale": (ctypes.c_int, [vp, vp, vp, u32, u32, vp, sz, vp]),
+            "catfhe_decrypt": (ctypes.c_int, [vp, vp, vp, u32, u64, vp, vp, sz, vp]),
+            "catfhe_ntt": (ctypes.c_int, [vp, vp, u32, u32, ctypes.c_int, vp]),
+            "catfhe_workspace_bytes": (sz, [vp, ctypes.c_int, u32, u32]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise CatfheError(rc, what)
+
+
+def _seed(seed: bytes):
+    assert len(seed) == 32
+    return (ctypes.c_uint8 * 32).from_buffer_copy(seed)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def params_from_preset(p: W.Preset) -> Params:
+    prm = Params()
+    prm.scheme, prm.log_n = p.scheme, p.log_n
+    prm.log_n_max = p.log_n_max or p.log_n
+    prm.L, prm.K, prm.dnum = p.L, p.K, p.dnum
+    for i, b in enumerate(p.q_bits):
+        prm.q_bits[i] = b
+    for i, b in enumerate(p.p_bits):
+        prm.p_bits[i] = b
+    prm.t = p.t
+    prm.aux_count = 0
+    prm.aux_bits = p.b_bits
+    return prm
+
+
+class Context:
+    """A parameter set on the current CUDA device (primes, NTT tables)."""
+
+    def __init__(self, preset: W.Preset | Params):
+        L = load()
+        prm = params_from_preset(preset) if isinstance(preset, W.Preset) else preset
+        self.preset = preset if isinstance(preset, W.Preset) else None
+        h = vp()
+        _check(L.catfhe_ctx_create(ctypes.byref(prm), ctypes.byref(h)), "catfhe_ctx_create")
+        self._h = h
+        info = Info()
+        _check(L.catfhe_ctx_info(h, ctypes.byref(info)), "catfhe_ctx_info")
+        self.n, self.L, self.K, self.nb = info.n, info.L, info.K, info.nb
+        self.alpha, self.beta = info.alpha, info.beta
+        self.scheme, self.t = prm.scheme, prm.t
+        q = (ctypes.c_uint64 * self.L)()
+        p = (ctypes.c_uint64 * self.K)()
+        b = (ctypes.c_uint64 * max(1, self.nb))()
+        _check(L.catfhe_ctx_moduli(h, q, p, b), "catfhe_ctx_moduli")
+        self.q, self.p, self.b = list(q), list(p), list(b)[: self.nb]
+        self._ws = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().catfhe_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- buffers
+    def empty_ct(self, count: int, level: int):
+        torch = _torch()
+        return torch.empty((count, 2, level, self.n), dtype=torch.int64, device="cuda")
+
+    def workspace(self, op: int, level: int, count: int):
+        torch = _torch()
+        need = load().catfhe_workspace_bytes(self._h, op, level, count)
+        key = (op, level, count)
+        ws = self._ws.get(key)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(max(need, 1), dtype=torch.uint8, device="cuda")
+            self._ws[key] = ws
+        return ws
+
+    def galois_elt(self, steps: int) -> int:
+        return int(load().catfhe_galois_elt(self._h, steps))
+
+    # ---------------------------------------------------------------- keys
+    def keygen(self, seed: bytes) -> "Keys":
+        return Keys(self, seed)
+
+    # ---------------------------------------------------------------- ciphertext I/O
+    def encrypt(self, keys: "Keys", msg: np.ndarray, seed: bytes):
+        m = np.ascontiguousarray(np.asarray(msg, dtype=np.int64))
+        assert m.shape == (self.n,)
+        out = self.empty_ct(1, self.L)
+        _check(load().catfhe_encrypt(self._h, keys._h, m.ctypes.data_as(vp), _seed(seed), _ptr(out),
+                                     _stream()), "catfhe_encrypt")
+        return out
+
+    def ct_uniform(self, seed: bytes, index: int, level: int):
+        out = self.empty_ct(1, level)
+        _check(load().catfhe_ct_uniform(self._h, _seed(seed), index, level, _ptr(out), _stream()),
+               "catfhe_ct_uniform")
+        return out
+
+    def import_ct(self, host: np.ndarray, form: int = FORM_COEFF):
+        """host: uint64 [count][2][level][N] -> device tensor (at-rest form)."""
+        h = np.ascontiguousarray(host, dtype=np.uint64)
+        if h.ndim == 3:
+            h = h[None]
+        count, _, level, _ = h.shape
+        out = self.empty_ct(count, level)
+        _check(load().catfhe_ct_import(self._h, h.ctypes.data_as(vp), level, count, form, _ptr(out),
+                                       _stream()), "catfhe_ct_import")
+        return out
+
+    def export_ct(self, ct, form: int = FORM_COEFF) -> np.ndarray:
+        count, _, level, n = ct.shape
+        host = np.empty((count, 2, level, n), dtype=np.uint64)
+        ws = self.workspace(OP_EXPORT, level, count)
+        _check(load().catfhe_ct_export(self._h, _ptr(ct), level, count, form, host.ctypes.data_as(vp),
+                                       _ptr(ws), ws.numel(), _stream()), "catfhe_ct_export")
+        return host
+
+    def decrypt(self, keys: "Keys", ct, factor: int = 1) -> np.ndarray:
+        level = ct.shape[-2]
+        out = np.empty(self.n, dtype=np.int64)
+        ws = self.workspace(OP_DECRYPT, level, 1)
+        _check(load().catfhe_decrypt(self._h, keys._h, _ptr(ct), level, factor, out.ctypes.data_as(vp),
+                                     _ptr(ws), ws.numel(), _stream()), "catfhe_decrypt")
+        return out
+
+    # ---------------------------------------------------------------- operations
+    def add(self, a, b, out=None):
+        count, _, level, _ = a.shape
+        out = self.empty_ct(count, level) if out is None else out
+        _check(load().catfhe_add(self._h, _ptr(a), _ptr(b), _ptr(out), level, count, _stream()),
+               "catfhe_add")
+        return out
+
+    def mul_relin(self, keys: "Keys", a, b, out=None):
+        count, _, level, _ = a.shape
+        out = self.empty_ct(count, level) if out is None else out
+        ws = self.workspace(OP_MUL_RELIN, level, count)
+        _check(load().catfhe_mul_relin(self._h, keys._h, _ptr(a), _ptr(b), _ptr(out), level, count,
+                                       _ptr(ws), ws.numel(), _stream()), "catfhe_mul_relin")
+        return out
+
+    def mul_relin_rescale(self, keys: "Keys", a, b, out=None):
+        count, _, level, _ = a.shape
+        out = self.empty_ct(count, level - 1) if out is None else out
+        ws = self.workspace(OP_MUL_RELIN_RESCALE, level, count)
+        _check(load().catfhe_mul_relin_rescale(self._h, keys._h, _ptr(a), _ptr(b), _ptr(out), level,
+                                               count, _ptr(ws), ws.numel(), _stream()),
+               "catfhe_mul_relin_rescale")
+        return out
+
+    def rotate(self, keys: "Keys", a, galois_elt: int, out=None):
+        count, _, level, _ = a.shape
+        out = self.empty_ct(count, level) if out is None else out
+        ws = self.workspace(OP_ROTATE, level, count)
+        _check(load().catfhe_rotate(self._h, keys._h, _ptr(a), galois_elt, _ptr(out), level, count,
+                                    _ptr(ws), ws.numel(), _stream()), "catfhe_rotate")
+        return out
+
+    def rescale(self, a, out=None):
+        count, _, level, _ = a.shape
+        out = self.empty_ct(count, level - 1) if out is None else out
+        ws = self.workspace(OP_RESCALE, level, count)
+        _check(load().catfhe_rescale(self._h, _ptr(a), _ptr(out), level, count, _ptr(ws), ws.numel(),
+                                     _stream()), "catfhe_rescale")
+        return out
+
+    def ntt(self, limbs, inverse: bool = False):
+        """limbs: int64 tensor [count][level][N], transformed in place."""
+        count, level, _ = limbs.shape
+        _check(load().catfhe_ntt(self._h, _ptr(limbs), level, count, int(inverse), _stream()),
+               "catfhe_ntt")
+        return limbs
+
+
+class Keys:
+    def __init__(self, ctx: Context, seed: bytes):
+        self.ctx = ctx
+        h = vp()
+        _check(load().catfhe_keygen(ctx._h, _seed(seed), ctypes.byref(h)), "catfhe_keygen")
+        self._h = h
+
+    def gen_galois(self, g: int) -> None:
+        _check(load().catfhe_gen_galois_key(self.ctx._h, self._h, g), "catfhe_gen_galois_key")
+
+    def export(self, key_id: int = 0, s=True, pk=True, ksk=True):
+        c = self.ctx
+        S = np.empty(c.n, dtype=np.int64) if s else None
+        PK = np.empty((2, c.L, c.n), dtype=np.uint64) if pk else None
+        KS = np.empty((c.beta, 2, c.L + c.K, c.n), dtype=np.uint64) if ksk else None
+        _check(load().catfhe_keys_export(c._h, self._h, key_id,
+                                         S.ctypes.data_as(vp) if s else None,
+                                         PK.ctypes.data_as(vp) if pk else None,
+                                         KS.ctypes.data_as(vp) if ksk else None), "catfhe_keys_export")
+        return S, PK, KS
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().catfhe_keys_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,228 @@
+// The C ABI (include/catfhe.h): argument checks and dispatch.
+#include <string.h>
+
+#include <new>
+
+#include "internal.h"
+
+struct catfhe_ctx {
+    catfhe::Context c;
+};
+struct catfhe_keys {
+    catfhe::Keys *k;
+    const catfhe_ctx *owner;
+};
+
+namespace catfhe {
+int ctx_init(Context &c, const catfhe_params &p);
+void ctx_free(Context &c);
+size_t ws_bytes(const Context &c, int op, uint32_t level, uint32_t count);
+int op_mul_relin(Context &c, const Keys &keys, const uint64_t *a, const uint64_t *b,
+                 uint64_t *out, uint32_t level, uint32_t count, bool fused, void *ws,
+                 size_t ws_bytes_in, cudaStream_t s);
+int op_rotate(Context &c, const Keys &keys, const uint64_t *a, uint64_t g, uint64_t *out,
+              uint32_t level, uint32_t count, void *ws, size_t ws_bytes_in, cudaStream_t s);
+int op_rescale(Context &c, const uint64_t *a, uint64_t *out, uint32_t level, uint32_t count,
+               void *ws, size_t ws_bytes_in, cudaStream_t s);
+int op_add(Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t level,
+           uint32_t count, cudaStream_t s);
+int op_ntt(Context &c, uint64_t *limbs, uint32_t level, uint32_t count, int inverse,
+           cudaStream_t s);
+int op_keygen(Context &c, const uint8_t seed[32], Keys **out);
+int op_gen_galois(Context &c, Keys &k, uint64_t g);
+void keys_free(Keys *k);
+int op_keys_export(Context &c, const Keys &k, uint64_t id, int64_t *s_out, uint64_t *pk_out,
+                   uint64_t *ksk_out);
+int op_encrypt(Context &c, const Keys &k, const int64_t *msg, const uint8_t seed[32],
+               uint64_t *ct, cudaStream_t s);
+int op_ct_uniform(Context &c, const uint8_t seed[32], uint32_t index, uint32_t level, uint64_t *ct,
+                  cudaStream_t s);
+int op_import(Context &c, const uint64_t *host, uint32_t level, uint32_t count, int form,
+              uint64_t *ct, cudaStream_t s);
+int op_export(Context &c, const uint64_t *ct, uint32_t level, uint32_t count, int form,
+              uint64_t *host, void *ws, size_t ws_bytes_in, cudaStream_t s);
+int op_decrypt(Context &c, const Keys &k, const uint64_t *ct, uint32_t level, uint64_t factor,
+               int64_t *msg, void *ws, size_t ws_bytes_in, cudaStream_t s);
+}  // namespace catfhe
+
+using namespace catfhe;
+
+static cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
+
+static bool keys_ok(const catfhe_ctx *ctx, const catfhe_keys *k) {
+    return ctx && k && k->k && k->owner == ctx;
+}
+
+extern "C" {
+
+const char *catfhe_strerror(int code) {
+    switch (code) {
+        case CATFHE_OK: return "ok";
+        case CATFHE_EINVAL: return "invalid argument";
+        case CATFHE_ELEVEL: return "level out of range";
+        case CATFHE_ENOKEY: return "key-switching key missing";
+        case CATFHE_ENOMEM: return "device allocation failed";
+        case CATFHE_ECUDA: return "CUDA error";
+        case CATFHE_ESCHEME: return "operation not defined for this scheme";
+        case CATFHE_EWORKSPACE: return "workspace too small";
+        default: return "unknown error";
+    }
+}
+
+int catfhe_ctx_create(const catfhe_params *params, catfhe_ctx **out) {
+    if (!params || !out) return CATFHE_EINVAL;
+    catfhe_ctx *ctx = new (std::nothrow) catfhe_ctx();
+    if (!ctx) return CATFHE_ENOMEM;
+    int rc = ctx_init(ctx->c, *params);
+    if (rc != CATFHE_OK) {
+        ctx_free(ctx->c);
+        delete ctx;
+        return rc;
+    }
+    *out = ctx;
+    return CATFHE_OK;
+}
+
+void catfhe_ctx_destroy(catfhe_ctx *ctx) {
+    if (!ctx) return;
+    ctx_free(ctx->c);
+    delete ctx;
+}
+
+int catfhe_ctx_info(const catfhe_ctx *ctx, catfhe_info *out) {
+    if (!ctx || !out) return CATFHE_EINVAL;
+    const Context &c = ctx->c;
+    out->n = int32_t(c.n);
+    out->L = c.L;
+    out->K = c.K;
+    out->nb = c.nb;
+    out->alpha = c.alpha;
+    out->beta = c.beta;
+    return CATFHE_OK;
+}
+
+int catfhe_ctx_moduli(const catfhe_ctx *ctx, uint64_t *q, uint64_t *p, uint64_t *b) {
+    if (!ctx) return CATFHE_EINVAL;
+    const Context &c = ctx->c;
+    for (int i = 0; i < c.L && q; i++) q[i] = c.mod(i);
+    for (int i = 0; i < c.K && p; i++) p[i] = c.mod(c.pp(i));
+    for (int i = 0; i < c.nb && b; i++) b[i] = c.mod(c.pb(i));
+    return CATFHE_OK;
+}
+
+uint64_t catfhe_galois_elt(const catfhe_ctx *ctx, int64_t steps) {
+    if (!ctx) return 0;
+    const uint64_t two_n = 2 * ctx->c.n, slots = ctx->c.n / 2;
+    int64_t r = steps % int64_t(slots);
+    if (r < 0) r += int64_t(slots);
+    return h_powmod(5, uint64_t(r), two_n);
+}
+
+int catfhe_keygen(catfhe_ctx *ctx, const uint8_t seed[32], catfhe_keys **out) {
+    if (!ctx || !seed || !out) return CATFHE_EINVAL;
+    Keys *k = nullptr;
+    int rc = op_keygen(ctx->c, seed, &k);
+    if (rc != CATFHE_OK) return rc;
+    catfhe_keys *h = new (std::nothrow) catfhe_keys{k, ctx};
+    if (!h) {
+        keys_free(k);
+        return CATFHE_ENOMEM;
+    }
+    *out = h;
+    return CATFHE_OK;
+}
+
+int catfhe_gen_galois_key(catfhe_ctx *ctx, catfhe_keys *keys, uint64_t galois_elt) {
+    if (!keys_ok(ctx, keys)) return CATFHE_EINVAL;
+    return op_gen_galois(ctx->c, *keys->k, galois_elt);
+}
+
+void catfhe_keys_destroy(catfhe_keys *keys) {
+    if (!keys) return;
+    keys_free(keys->k);
+    delete keys;
+}
+
+int catfhe_keys_export(catfhe_ctx *ctx, const catfhe_keys *keys, uint64_t key_id, int64_t *s,
+                       uint64_t *pk, uint64_t *ksk) {
+    if (!keys_ok(ctx, keys)) return CATFHE_EINVAL;
+    return op_keys_export(ctx->c, *keys->k, key_id, s, pk, ksk);
+}
+
+int catfhe_encrypt(catfhe_ctx *ctx, const catfhe_keys *keys, const int64_t *msg,
+                   const uint8_t seed[32], uint64_t *ct, void *stream) {
+    if (!keys_ok(ctx, keys) || !msg || !seed || !ct) return CATFHE_EINVAL;
+    return op_encrypt(ctx->c, *keys->k, msg, seed, ct, S(stream));
+}
+
+int catfhe_ct_uniform(catfhe_ctx *ctx, const uint8_t seed[32], uint32_t index, uint32_t level,
+                      uint64_t *ct, void *stream) {
+    if (!ctx || !seed || !ct) return CATFHE_EINVAL;
+    return op_ct_uniform(ctx->c, seed, index, level, ct, S(stream));
+}
+
+int catfhe_ct_import(catfhe_ctx *ctx, const uint64_t *host, uint32_t level, uint32_t count,
+                     int form, uint64_t *ct, void *stream) {
+    if (!ctx || !host || !ct || (form != CATFHE_FORM_COEFF && form != CATFHE_FORM_NATIVE))
+        return CATFHE_EINVAL;
+    return op_import(ctx->c, host, level, count, form, ct, S(stream));
+}
+
+int catfhe_ct_export(catfhe_ctx *ctx, const uint64_t *ct, uint32_t level, uint32_t count,
+                     int form, uint64_t *host, void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx || !host || !ct || (form != CATFHE_FORM_COEFF && form != CATFHE_FORM_NATIVE))
+        return CATFHE_EINVAL;
+    return op_export(ctx->c, ct, level, count, form, host, ws, ws_bytes, S(stream));
+}
+
+int catfhe_add(catfhe_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out,
+               uint32_t level, uint32_t count, void *stream) {
+    if (!ctx || !a || !b || !out) return CATFHE_EINVAL;
+    return op_add(ctx->c, a, b, out, level, count, S(stream));
+}
+
+int catfhe_mul_relin(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
+                     const uint64_t *b, uint64_t *out, uint32_t level, uint32_t count,
+                     void *ws, size_t ws_bytes, void *stream) {
+    if (!keys_ok(ctx, keys) || !a || !b || !out) return CATFHE_EINVAL;
+    return op_mul_relin(ctx->c, *keys->k, a, b, out, level, count, false, ws, ws_bytes, S(stream));
+}
+
+int catfhe_mul_relin_rescale(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
+                             const uint64_t *b, uint64_t *out, uint32_t level, uint32_t count,
+                             void *ws, size_t ws_bytes, void *stream) {
+    if (!keys_ok(ctx, keys) || !a || !b || !out) return CATFHE_EINVAL;
+    return op_mul_relin(ctx->c, *keys->k, a, b, out, level, count, true, ws, ws_bytes, S(stream));
+}
+
+int catfhe_rotate(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
+                  uint64_t galois_elt, uint64_t *out, uint32_t level, uint32_t count, void *ws,
+                  size_t ws_bytes, void *stream) {
+    if (!keys_ok(ctx, keys) || !a || !out) return CATFHE_EINVAL;
+    return op_rotate(ctx->c, *keys->k, a, galois_elt, out, level, count, ws, ws_bytes, S(stream));
+}
+
+int catfhe_rescale(catfhe_ctx *ctx, const uint64_t *a, uint64_t *out, uint32_t level,
+                   uint32_t count, void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx || !a || !out) return CATFHE_EINVAL;
+    return op_rescale(ctx->c, a, out, level, count, ws, ws_bytes, S(stream));
+}
+
+int catfhe_decrypt(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *ct, uint32_t level,
+                   uint64_t factor, int64_t *msg, void *ws, size_t ws_bytes, void *stream) {
+    if (!keys_ok(ctx, keys) || !ct || !msg) return CATFHE_EINVAL;
+    return op_decrypt(ctx->c, *keys->k, ct, level, factor, msg, ws, ws_bytes, S(stream));
+}
+
+int catfhe_ntt(catfhe_ctx *ctx, uint64_t *limbs, uint32_t level, uint32_t count, int inverse,
+               void *stream) {
+    if (!ctx || !limbs) return CATFHE_EINVAL;
+    return op_ntt(ctx->c, limbs, level, count, inverse, S(stream));
+}
+
+size_t catfhe_workspace_bytes(const catfhe_ctx *ctx, int op, uint32_t level, uint32_t count) {
+    if (!ctx) return 0;
+    return ws_bytes(ctx->c, op, level, count);
+}
+
+}  // extern "C"

@@ -1,0 +1,398 @@
+// Element-wise kernels of the hot path: the fused tensor product (paper
+// Sec. 3.1.4: the four products and the middle sum of a CKKS multiply in one
+// kernel), the key-switching inner product, the ModDown combine, the
+// automorphism X -> X^g, and ChaCha20 sampling for keys and encryption.
+//
+// All are HBM-bound streams over limb-major data: one thread per coefficient,
+// consecutive threads on consecutive words, grids sized by the data (a whole
+// batch of ciphertexts per launch).
+#include "modarith.cuh"
+
+namespace catfhe {
+
+static inline int ok() { return cudaGetLastError() == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA; }
+
+static inline dim3 coeff_grid(size_t n, uint32_t y, uint32_t z = 1) {
+    return dim3(unsigned((n + 255) / 256), y, z);
+}
+
+// ------------------------------------------------------------------ tensor
+
+__global__ void __launch_bounds__(256)
+k_tensor(const TensorArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint32_t i = blockIdx.y, item = blockIdx.z;
+    if (x >= n) return;
+    const DevMod m = mods[A.prime[i]];
+    const uint64_t *a = A.a + item * A.in_item, *b = A.b + item * A.in_item;
+    const size_t l0 = size_t(i) * n + x, l1 = (size_t(A.limbs) + i) * n + x;
+    const uint64_t a0 = a[l0], a1 = a[l1], b0 = b[l0], b1 = b[l1];
+    const size_t o = item * A.out_item + size_t(i) * n + x;
+    A.d0[o] = mul_mod(a0, b0, m);
+    U128 acc{0, 0};
+    mac(acc, a0, b1);
+    mac(acc, a1, b0);
+    A.d1[o] = reduce128(acc, m);
+    A.d2[o] = mul_mod(a1, b1, m);
+}
+
+int launch_tensor(const Context &c, const TensorArgs &a, uint32_t count, cudaStream_t s) {
+    k_tensor<<<coeff_grid(c.n, a.limbs, count), 256, 0, s>>>(a, c.d_mods, c.log_n);
+    return ok();
+}
+
+// ------------------------------------------------------------------ key-switch inner product
+
+// y_p[i] = sum_j c_j[i] * key_j[p][i] (+ P * add_p[i] on ciphertext primes).
+__global__ void __launch_bounds__(256)
+k_ip(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint32_t i = blockIdx.y, item = blockIdx.z;
+    if (x >= n) return;
+    const DevMod m = mods[A.prime[i]];
+    const uint32_t KL = A.L + A.K;
+    const uint64_t *ext = A.ext + item * A.ext_item;
+    const bool own_here = A.own != nullptr && i < A.level;
+    const uint32_t own_digit = own_here ? i / A.alpha : 0xffffffffu;
+    U128 acc0{0, 0}, acc1{0, 0};
+    for (uint32_t j = 0; j < A.beta; j++) {
+        const uint64_t cj = (j == own_digit) ? A.own[item * A.own_item + size_t(i) * n + x]
+                                             : ext[(size_t(j) * A.M + i) * n + x];
+        const uint64_t kb = A.key[((size_t(j) * 2 + 0) * KL + A.key_limb[i]) * n + x];
+        const uint64_t ka = A.key[((size_t(j) * 2 + 1) * KL + A.key_limb[i]) * n + x];
+        mac(acc0, cj, kb);
+        mac(acc1, cj, ka);
+    }
+    uint64_t y0 = reduce128(acc0, m), y1 = reduce128(acc1, m);
+    if (i < A.level && A.pfac[i] != 0) {
+        if (A.add0)
+            y0 = add_mod(y0, shoup(A.add0[item * A.add_item + size_t(i) * n + x], A.pfac[i],
+                                   A.pfac_s[i], m.q), m.q);
+        if (A.add1)
+            y1 = add_mod(y1, shoup(A.add1[item * A.add_item + size_t(i) * n + x], A.pfac[i],
+                                   A.pfac_s[i], m.q), m.q);
+    }
+    uint64_t *y = A.y + item * A.y_item;
+    y[size_t(i) * n + x] = y0;
+    y[(size_t(A.M) + i) * n + x] = y1;
+}
+
+int launch_ip(const Context &c, const IpArgs &a, uint32_t count, cudaStream_t s) {
+    k_ip<<<coeff_grid(c.n, a.M, count), 256, 0, s>>>(a, c.d_mods, c.log_n);
+    return ok();
+}
+
+// ------------------------------------------------------------------ ModDown combine
+
+// out_p[i] = (y_p[i] - lift_p[i]) * D^-1 (+ add_p[i]).
+__global__ void __launch_bounds__(256)
+k_combine(const CombineArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint32_t i = blockIdx.y % A.lo, p = blockIdx.y / A.lo, item = blockIdx.z;
+    if (x >= n) return;
+    const uint64_t q = mods[A.prime[i]].q;
+    const uint64_t y = A.y[item * A.y_item + p * A.y_poly + size_t(i) * n + x];
+    const uint64_t l = A.lift[item * A.lift_item + p * A.lift_poly + size_t(i) * n + x];
+    uint64_t r = shoup(y + q - l, A.dinv[i], A.dinv_s[i], q);
+    if (A.add) r = add_mod(r, A.add[item * A.add_item + p * A.add_poly + size_t(i) * n + x], q);
+    A.out[item * A.out_item + p * A.out_poly + size_t(i) * n + x] = r;
+}
+
+int launch_combine(const Context &c, const CombineArgs &a, uint32_t count, cudaStream_t s) {
+    k_combine<<<coeff_grid(c.n, 2 * a.lo, count), 256, 0, s>>>(a, c.d_mods, c.log_n);
+    return ok();
+}
+
+// ------------------------------------------------------------------ automorphism
+
+// NTT form: slot k = bitrev(i) holds a(psi^(2i+1)); sigma_g(a) there is
+// a(psi^((2i+1) g)), a pure permutation of the slots.
+__global__ void __launch_bounds__(256)
+k_automorph_ntt(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, uint64_t g,
+                uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t k = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint64_t mask2n = 2 * n - 1;
+    const uint32_t i = __brev(uint32_t(k)) >> (32 - log_n);
+    const uint64_t e = ((2 * uint64_t(i) + 1) * g) & mask2n;
+    const uint32_t src = __brev(uint32_t((e - 1) >> 1)) >> (32 - log_n);
+    const size_t limb = blockIdx.y;
+    out[limb * n + k] = in[limb * n + src];
+}
+
+int launch_automorph_ntt(const Context &c, const uint64_t *in, uint64_t *out, uint32_t limbs_total,
+                         uint64_t g, cudaStream_t s) {
+    k_automorph_ntt<<<coeff_grid(c.n, limbs_total), 256, 0, s>>>(in, out, g % (2 * c.n), c.log_n);
+    return ok();
+}
+
+// Coefficient form: out[k] = +in[i] if i g = k (mod 2N), -in[i] if i g = k + N.
+__global__ void __launch_bounds__(256)
+k_automorph_coeff(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, const LimbMap map,
+                  const DevMod *__restrict__ mods, uint64_t ginv, uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t k = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t limb = blockIdx.y, g = limb / map.period, r = limb % map.period;
+    const uint64_t *src = in + (size_t(g) * map.src_stride + map.src_off[r]) * n;
+    uint64_t *dst = out + (size_t(g) * map.dst_stride + map.dst_off[r]) * n;
+    const uint64_t q = mods[map.prime[r]].q;
+    const uint64_t i1 = (uint64_t(k) * ginv) & (2 * n - 1);
+    if (i1 < n) {
+        dst[k] = src[i1];
+    } else {
+        const uint64_t v = src[i1 - n];
+        dst[k] = v ? q - v : 0;
+    }
+}
+
+static uint64_t inv_mod_pow2(uint64_t g, uint64_t two_n) {
+    // g odd: Newton iteration for the inverse modulo a power of two
+    uint64_t x = g;
+    for (int i = 0; i < 6; i++) x *= 2 - g * x;
+    return x & (two_n - 1);
+}
+
+int launch_automorph_coeff(const Context &c, const uint64_t *in, uint64_t *out,
+                           const LimbMap &map, uint32_t n_limbs, uint64_t g, cudaStream_t s) {
+    const uint64_t ginv = inv_mod_pow2(g % (2 * c.n), 2 * c.n);
+    k_automorph_coeff<<<coeff_grid(c.n, n_limbs), 256, 0, s>>>(in, out, map, c.d_mods, ginv,
+                                                               c.log_n);
+    return ok();
+}
+
+// ------------------------------------------------------------------ simple maps
+
+__global__ void __launch_bounds__(256)
+k_add(const uint64_t *__restrict__ a, const uint64_t *__restrict__ b, uint64_t *out,
+      const LimbMap map, const DevMod *__restrict__ mods, uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const uint32_t limb = blockIdx.y, g = limb / map.period, r = limb % map.period;
+    const size_t o = (size_t(g) * map.src_stride + map.src_off[r]) * n + x;
+    out[o] = add_mod(a[o], b[o], mods[map.prime[r]].q);
+}
+
+int launch_add(const Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out,
+               const LimbMap &map, uint32_t n_limbs, cudaStream_t s) {
+    k_add<<<coeff_grid(c.n, n_limbs), 256, 0, s>>>(a, b, out, map, c.d_mods, c.log_n);
+    return ok();
+}
+
+__global__ void __launch_bounds__(256)
+k_copy(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, const LimbMap map,
+       uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const uint32_t limb = blockIdx.y, g = limb / map.period, r = limb % map.period;
+    dst[(size_t(g) * map.dst_stride + map.dst_off[r]) * n + x] =
+        src[(size_t(g) * map.src_stride + map.src_off[r]) * n + x];
+}
+
+int launch_copy_limbs(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
+                      uint32_t n_limbs, cudaStream_t s) {
+    k_copy<<<coeff_grid(c.n, n_limbs), 256, 0, s>>>(src, dst, map, c.log_n);
+    return ok();
+}
+
+__global__ void __launch_bounds__(256)
+k_pointwise(const uint64_t *__restrict__ a, const uint64_t *__restrict__ b, uint64_t *out,
+            const LimbMap map, const DevMod *__restrict__ mods, uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const uint32_t limb = blockIdx.y, g = limb / map.period, r = limb % map.period;
+    const size_t ia = (size_t(g) * map.src_stride + map.src_off[r]) * n + x;
+    const size_t io = (size_t(g) * map.dst_stride + map.dst_off[r]) * n + x;
+    out[io] = mul_mod(a[ia], b[io], mods[map.prime[r]]);
+}
+
+// out[dst] = a[src] * b[dst] over the map
+int launch_pointwise(const Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out,
+                     const LimbMap &map, uint32_t n_limbs, cudaStream_t s) {
+    k_pointwise<<<coeff_grid(c.n, n_limbs), 256, 0, s>>>(a, b, out, map, c.d_mods, c.log_n);
+    return ok();
+}
+
+// out[i] = c0[i] + c1[i] * sk[i] (or c0 - c1 sk), limbs 0..limbs-1 mod q_i.
+__global__ void __launch_bounds__(256)
+k_mul_add(const uint64_t *__restrict__ c0, const uint64_t *__restrict__ c1,
+          const uint64_t *__restrict__ sk, uint64_t *out, int negate,
+          const DevMod *__restrict__ mods, uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const uint32_t i = blockIdx.y;
+    const DevMod m = mods[i];
+    const size_t o = size_t(i) * n + x;
+    const uint64_t prod = mul_mod(c1[o], sk[o], m);
+    const uint64_t base = c0 ? c0[o] : 0;
+    out[o] = negate ? sub_mod(base, prod, m.q) : add_mod(base, prod, m.q);
+}
+
+int launch_mul_add(const Context &c, const uint64_t *c0, const uint64_t *c1, const uint64_t *sk,
+                   uint64_t *out, uint32_t limbs, int negate_product, cudaStream_t s) {
+    k_mul_add<<<coeff_grid(c.n, limbs), 256, 0, s>>>(c0, c1, sk, out, negate_product, c.d_mods,
+                                                     c.log_n);
+    return ok();
+}
+
+// b[i] = -a[i] sk[i] + e[i] + pfac_i sp[i] (NTT form, limbs of Q_L u P).
+__global__ void __launch_bounds__(256)
+k_ksk_row(const uint64_t *__restrict__ a, const uint64_t *__restrict__ sk,
+          const uint64_t *__restrict__ e, const uint64_t *__restrict__ sp, uint64_t *b,
+          const uint64_t *__restrict__ pfac, const uint64_t *__restrict__ pfac_s,
+          const DevMod *__restrict__ mods, uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const uint32_t i = blockIdx.y;
+    const DevMod m = mods[i];
+    const size_t o = size_t(i) * n + x;
+    uint64_t v = sub_mod(e[o], mul_mod(a[o], sk[o], m), m.q);
+    if (pfac[i]) v = add_mod(v, shoup(sp[o], pfac[i], pfac_s[i], m.q), m.q);
+    b[o] = v;
+}
+
+int launch_ksk_row(const Context &c, const uint64_t *a, const uint64_t *sk, const uint64_t *e,
+                   const uint64_t *sp, uint64_t *b, uint32_t limbs, const uint64_t *pfac,
+                   const uint64_t *pfac_s, cudaStream_t s) {
+    k_ksk_row<<<coeff_grid(c.n, limbs), 256, 0, s>>>(a, sk, e, sp, b, pfac, pfac_s, c.d_mods,
+                                                     c.log_n);
+    return ok();
+}
+
+// ------------------------------------------------------------------ sampling
+
+__device__ __forceinline__ uint32_t rotl(uint32_t x, int r) { return (x << r) | (x >> (32 - r)); }
+
+#define QR(a, b, c, d)                     \
+    a += b; d ^= a; d = rotl(d, 16);       \
+    c += d; b ^= c; b = rotl(b, 12);       \
+    a += b; d ^= a; d = rotl(d, 8);        \
+    c += d; b ^= c; b = rotl(b, 7);
+
+// One ChaCha20 block (RFC 8439 Sec. 2.3): 16 output words.
+__device__ __forceinline__ void chacha_block(const SampleArgs &A, uint32_t counter, uint32_t out[16]) {
+    uint32_t s[16];
+    s[0] = 0x61707865u; s[1] = 0x3320646eu; s[2] = 0x79622d32u; s[3] = 0x6b206574u;
+#pragma unroll
+    for (int i = 0; i < 8; i++) s[4 + i] = A.key[i];
+    s[12] = counter; s[13] = A.tag; s[14] = A.i0; s[15] = A.i1;
+    uint32_t x[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) x[i] = s[i];
+#pragma unroll 1
+    for (int r = 0; r < 10; r++) {
+        QR(x[0], x[4], x[8], x[12]);
+        QR(x[1], x[5], x[9], x[13]);
+        QR(x[2], x[6], x[10], x[14]);
+        QR(x[3], x[7], x[11], x[15]);
+        QR(x[0], x[5], x[10], x[15]);
+        QR(x[1], x[6], x[11], x[12]);
+        QR(x[2], x[7], x[8], x[13]);
+        QR(x[3], x[4], x[9], x[14]);
+    }
+#pragma unroll
+    for (int i = 0; i < 16; i++) out[i] = x[i] + s[i];
+}
+#undef QR
+
+// word w of the keystream = little-endian bytes 8w..8w+7: block w/8,
+// 32-bit words 2(w%8) (low) and 2(w%8)+1 (high).
+__global__ void __launch_bounds__(256)
+k_sample(const SampleArgs A, uint64_t *out, const LimbMap map, const DevMod *__restrict__ mods,
+         const uint64_t *__restrict__ mult, const uint64_t *__restrict__ mult_s, uint32_t n_limbs,
+         uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t blk = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    uint32_t o[16];
+    if (A.kind == kUniform) {
+        // block b covers coefficients k = 4b .. 4b+3 (k = limb * N + j)
+        if (blk * 4 >= size_t(n_limbs) * n) return;
+        chacha_block(A, uint32_t(blk), o);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const size_t k = blk * 4 + u;
+            const uint32_t r = uint32_t(k / n);
+            const size_t j = k % n;
+            const uint64_t hi = uint64_t(o[4 * u]) | (uint64_t(o[4 * u + 1]) << 32);
+            const uint64_t lo = uint64_t(o[4 * u + 2]) | (uint64_t(o[4 * u + 3]) << 32);
+            const DevMod m = mods[map.prime[r % map.period]];
+            const uint32_t g = r / map.period, rr = r % map.period;
+            out[(size_t(g) * map.dst_stride + map.dst_off[rr]) * n + j] = reduce128(U128{lo, hi}, m);
+        }
+        return;
+    }
+    // block b covers coefficients j = 8b .. 8b+7 of the small polynomial
+    if (blk * 8 >= n) return;
+    chacha_block(A, uint32_t(blk), o);
+    int64_t v[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+        const uint64_t w = uint64_t(o[2 * u]) | (uint64_t(o[2 * u + 1]) << 32);
+        if (A.kind == kTernary) {
+            v[u] = int64_t(w % 3) - 1;
+        } else {
+            const uint64_t low = w & ((uint64_t(1) << 40) - 1);
+            int64_t mag = 0;
+#pragma unroll
+            for (int t = 0; t < 19; t++) mag += (low >= A.cdt[t]) ? 1 : 0;
+            v[u] = (w >> 63) ? -mag : mag;
+        }
+    }
+    for (uint32_t l = 0; l < n_limbs; l++) {
+        const uint32_t g = l / map.period, rr = l % map.period;
+        const DevMod m = mods[map.prime[rr]];
+        uint64_t *dst = out + (size_t(g) * map.dst_stride + map.dst_off[rr]) * n + blk * 8;
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            uint64_t r = v[u] < 0 ? m.q - uint64_t(-v[u]) : uint64_t(v[u]);
+            if (mult) r = shoup(r, mult[rr], mult_s[rr], m.q);
+            dst[u] = r;
+        }
+    }
+}
+
+int launch_sample(const Context &c, const SampleArgs &a, uint64_t *out, const LimbMap &map,
+                  uint32_t n_limbs, const uint64_t *mult, const uint64_t *mult_s,
+                  cudaStream_t s) {
+    size_t blocks = a.kind == kUniform ? (size_t(n_limbs) * c.n + 3) / 4 : (c.n + 7) / 8;
+    k_sample<<<unsigned((blocks + 255) / 256), 256, 0, s>>>(a, out, map, c.d_mods, mult, mult_s,
+                                                            n_limbs, c.log_n);
+    return ok();
+}
+
+// int64 coefficients -> residues (times mult), optionally added to out.
+__global__ void __launch_bounds__(256)
+k_small_to_rns(const int64_t *__restrict__ in, uint64_t *out, const LimbMap map,
+               const DevMod *__restrict__ mods, const uint64_t *__restrict__ mult,
+               const uint64_t *__restrict__ mult_s, int accumulate, uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const uint32_t limb = blockIdx.y, g = limb / map.period, r = limb % map.period;
+    const DevMod m = mods[map.prime[r]];
+    const int64_t v = in[x];
+    uint64_t res = v < 0 ? m.q - reduce64(uint64_t(-(v + 1)) + 1, m) : reduce64(uint64_t(v), m);
+    res = csub(res, m.q);
+    if (mult) res = shoup(res, mult[r], mult_s[r], m.q);
+    uint64_t *o = out + (size_t(g) * map.dst_stride + map.dst_off[r]) * n + x;
+    *o = accumulate ? add_mod(*o, res, m.q) : res;
+}
+
+int launch_small_to_rns(const Context &c, const int64_t *in, uint64_t *out, const LimbMap &map,
+                        uint32_t n_limbs, const uint64_t *mult, const uint64_t *mult_s,
+                        int accumulate, cudaStream_t s) {
+    k_small_to_rns<<<coeff_grid(c.n, n_limbs), 256, 0, s>>>(in, out, map, c.d_mods, mult, mult_s,
+                                                           accumulate, c.log_n);
+    return ok();
+}
+
+}  // namespace catfhe

@@ -1,0 +1,65 @@
+// Modular arithmetic on 64-bit words for moduli q < 2^62 (device side).
+//
+// Products by a constant use Shoup's method: with w' = floor(w 2^64 / q),
+// a*w - floor(a*w' / 2^64)*q lies in [0, 2q) for every 64-bit a.  Sums of
+// products are accumulated exactly in 128 bits and reduced once: a 128-bit
+// x = hi 2^64 + lo is congruent to hi*(2^64 mod q) + lo*1, both terms by
+// Shoup, so the reduction needs only precomputed per-modulus constants.
+#pragma once
+
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace catfhe {
+
+__device__ __forceinline__ uint64_t mulhi(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
+
+__device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t q) { return x >= q ? x - q : x; }
+
+__device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q) {
+    return csub(a + b, q);
+}
+
+__device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) {
+    return csub(a + q - b, q);
+}
+
+// a*w mod q in [0, 2q); any 64-bit a, w < q, ws = floor(w 2^64 / q).
+__device__ __forceinline__ uint64_t shoup_lazy(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
+    return a * w - mulhi(a, ws) * q;
+}
+
+__device__ __forceinline__ uint64_t shoup(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
+    return csub(shoup_lazy(a, w, ws, q), q);
+}
+
+struct U128 {
+    uint64_t lo, hi;
+};
+
+__device__ __forceinline__ void mac(U128 &acc, uint64_t a, uint64_t b) {
+    uint64_t lo = a * b, hi = mulhi(a, b);
+    acc.lo += lo;
+    acc.hi += hi + (acc.lo < lo ? 1 : 0);
+}
+
+// Exact x mod q for any 128-bit x.
+__device__ __forceinline__ uint64_t reduce128(U128 x, const DevMod &m) {
+    uint64_t r = shoup_lazy(x.hi, m.r64, m.r64_s, m.q) + shoup_lazy(x.lo, 1, m.one_s, m.q);
+    r = csub(r, 2 * m.q);
+    return csub(r, m.q);
+}
+
+// a*b mod q for a, b < 2^64 (exact).
+__device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, const DevMod &m) {
+    U128 x{a * b, mulhi(a, b)};
+    return reduce128(x, m);
+}
+
+// x mod q for any 64-bit x.
+__device__ __forceinline__ uint64_t reduce64(uint64_t x, const DevMod &m) {
+    return csub(shoup_lazy(x, 1, m.one_s, m.q), m.q);
+}
+
+}  // namespace catfhe

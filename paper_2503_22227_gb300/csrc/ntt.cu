@@ -1,0 +1,322 @@
+// Batched negacyclic NTT / inverse NTT over 64-bit primes (paper Sec.
+// 3.1.3, the butterfly NTT "NTT_BM"), for N = 2^12 .. 2^16.
+//
+// Definition: out[bitrev(i)] = sum_j a_j psi^((2i+1) j) mod q.  Computed by
+// Cooley-Tukey butterflies with twiddles psi^bitrev(m + i) at stage
+// log2(m) (Gentleman-Sande with inverse twiddles for the inverse, N^-1
+// folded into its last stage).
+//
+// GB300 layout.  A limb of N = 2^16 words is 512 KiB, more than one CTA's
+// shared memory, so every transform is two passes over HBM:
+//  - column pass: the first k1 stages only mix the 2^k1 elements that
+//    share their low log N - k1 index bits (a strided "column"); a CTA
+//    loads CW adjacent columns (coalesced rows of CW words) and runs the
+//    k1 stages;
+//  - row pass: the remaining k2 = log N - k1 stages act inside contiguous
+//    chunks of 2^k2 words; a CTA loads several chunks.
+// Inside a pass every thread holds E = 2^LOGE words in registers and runs
+// LOGE stages on them without synchronisation; one shared-memory exchange
+// regroups the words for the remaining (<= LOGE) stages.  The grid spans
+// every limb of the batch (blockIdx.y), so one launch covers a whole batch
+// of ciphertexts: no per-modulus kernels or streams (the paper's kernel
+// segmentation, Sec. 3.1.4, is replaced by batching).
+#include "modarith.cuh"
+
+namespace catfhe {
+
+__device__ __forceinline__ void ct_bfly(uint64_t &a, uint64_t &b, ulonglong2 w, uint64_t q) {
+    const uint64_t t = shoup(b, w.x, w.y, q);
+    const uint64_t a0 = a;
+    a = add_mod(a0, t, q);
+    b = sub_mod(a0, t, q);
+}
+
+__device__ __forceinline__ void gs_bfly(uint64_t &a, uint64_t &b, ulonglong2 w, uint64_t q) {
+    const uint64_t a0 = a, b0 = b;
+    a = add_mod(a0, b0, q);
+    b = shoup(a0 + q - b0, w.x, w.y, q);
+}
+
+// ------------------------------------------------------------------ forward
+
+template <int LOGR, int LOGE>
+__global__ void __launch_bounds__(256)
+k_ntt_fwd_cols(const uint64_t *src, uint64_t *dst, const LimbMap map,
+               const DevMod *__restrict__ mods, const ulonglong2 *__restrict__ tw, int log_n) {
+    constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CW = 256 / T;
+    __shared__ uint64_t sm[R * CW];
+    const uint32_t limb = blockIdx.y;
+    const uint32_t g = limb / map.period, r = limb % map.period;
+    const size_t N = size_t(1) << log_n;
+    const size_t S = N >> LOGR;
+    const uint64_t *in = src + (size_t(g) * map.src_stride + map.src_off[r]) * N;
+    uint64_t *out = dst + (size_t(g) * map.dst_stride + map.dst_off[r]) * N;
+    const int p = map.prime[r];
+    const uint64_t q = mods[p].q;
+    const ulonglong2 *w = tw + size_t(p) * N;
+    const int cl = threadIdx.x % CW, tau = threadIdx.x / CW;
+    const size_t c = size_t(blockIdx.x) * CW + cl;
+
+    uint64_t x[E];
+#pragma unroll
+    for (int v = 0; v < E; v++) x[v] = in[c + size_t(tau + T * v) * S];
+    // stages 0 .. LOGE-1: partners at distance T*half are in this thread
+#pragma unroll
+    for (int st = 0; st < LOGE; st++) {
+        const int half = E >> (st + 1);
+#pragma unroll
+        for (int v = 0; v < E; v++) {
+            if (v & half) continue;
+            ct_bfly(x[v], x[v + half], w[(1 << st) + (v >> (LOGE - st))], q);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < E; v++) sm[(tau + T * v) * CW + cl] = x[v];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < E; v++) x[v] = sm[(tau * E + v) * CW + cl];
+    // stages LOGE .. LOGR-1: partners at distance < E
+#pragma unroll
+    for (int st = LOGE; st < LOGR; st++) {
+        const int dist = 1 << (LOGR - 1 - st);
+#pragma unroll
+        for (int v = 0; v < E; v++) {
+            if (v & dist) continue;
+            const int rr = tau * E + v;
+            ct_bfly(x[v], x[v + dist], w[(1 << st) + (rr >> (LOGR - st))], q);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < E; v++) out[c + size_t(tau * E + v) * S] = x[v];
+}
+
+template <int LOGR, int LOGE>
+__global__ void __launch_bounds__(256)
+k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__restrict__ mods,
+               const ulonglong2 *__restrict__ tw, int log_n) {
+    constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CC = 256 / T;
+    constexpr int RP = R + R / E;
+    __shared__ uint64_t sm[CC * RP];
+    const uint32_t limb = blockIdx.y;
+    const uint32_t g = limb / map.period, r = limb % map.period;
+    const size_t N = size_t(1) << log_n;
+    uint64_t *out = data + (size_t(g) * map.dst_stride + map.dst_off[r]) * N;
+    const int p = map.prime[r];
+    const uint64_t q = mods[p].q;
+    const ulonglong2 *w = tw + size_t(p) * N;
+    const int k1 = log_n - LOGR;
+    const int chl = threadIdx.x / T, tau = threadIdx.x % T;
+    const size_t h = size_t(blockIdx.x) * CC + chl;
+    uint64_t *base = out + h * R;
+    uint64_t *s = sm + chl * RP;
+#define PAD(u) ((u) + ((u) >> LOGE))
+
+    uint64_t x[E];
+#pragma unroll
+    for (int v = 0; v < E; v++) x[v] = base[tau + T * v];
+#pragma unroll
+    for (int st = 0; st < LOGE; st++) {
+        const int half = E >> (st + 1);
+#pragma unroll
+        for (int v = 0; v < E; v++) {
+            if (v & half) continue;
+            const size_t idx = (size_t(1) << (k1 + st)) + (h << st) + (v >> (LOGE - st));
+            ct_bfly(x[v], x[v + half], w[idx], q);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < E; v++) s[PAD(tau + T * v)] = x[v];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < E; v++) x[v] = s[PAD(tau * E + v)];
+#pragma unroll
+    for (int st = LOGE; st < LOGR; st++) {
+        const int dist = 1 << (LOGR - 1 - st);
+#pragma unroll
+        for (int v = 0; v < E; v++) {
+            if (v & dist) continue;
+            const int u = tau * E + v;
+            const size_t idx = (size_t(1) << (k1 + st)) + (h << st) + (u >> (LOGR - st));
+            ct_bfly(x[v], x[v + dist], w[idx], q);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < E; v++) s[PAD(tau * E + v)] = x[v];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < E; v++) base[tau + T * v] = s[PAD(tau + T * v)];
+#undef PAD
+}
+
+// ------------------------------------------------------------------ inverse
+
+template <int LOGR, int LOGE>
+__global__ void __launch_bounds__(256)
+k_ntt_inv_rows(const uint64_t *src, uint64_t *dst, const LimbMap map,
+               const DevMod *__restrict__ mods, const ulonglong2 *__restrict__ tw, int log_n) {
+    constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CC = 256 / T;
+    constexpr int RP = R + R / E;
+    __shared__ uint64_t sm[CC * RP];
+    const uint32_t limb = blockIdx.y;
+    const uint32_t g = limb / map.period, r = limb % map.period;
+    const size_t N = size_t(1) << log_n;
+    const uint64_t *in = src + (size_t(g) * map.src_stride + map.src_off[r]) * N;
+    uint64_t *out = dst + (size_t(g) * map.dst_stride + map.dst_off[r]) * N;
+    const int p = map.prime[r];
+    const uint64_t q = mods[p].q;
+    const ulonglong2 *w = tw + size_t(p) * N;
+    const int k1 = log_n - LOGR;
+    const int chl = threadIdx.x / T, tau = threadIdx.x % T;
+    const size_t h = size_t(blockIdx.x) * CC + chl;
+    uint64_t *s = sm + chl * RP;
+#define PAD(u) ((u) + ((u) >> LOGE))
+
+    uint64_t x[E];
+#pragma unroll
+    for (int v = 0; v < E; v++) s[PAD(tau + T * v)] = in[h * R + tau + T * v];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < E; v++) x[v] = s[PAD(tau * E + v)];
+    // stages LOGR-1 .. LOGE (distances 1 .. E/2)
+#pragma unroll
+    for (int st = LOGR - 1; st >= LOGE; st--) {
+        const int dist = 1 << (LOGR - 1 - st);
+#pragma unroll
+        for (int v = 0; v < E; v++) {
+            if (v & dist) continue;
+            const int u = tau * E + v;
+            const size_t idx = (size_t(1) << (k1 + st)) + (h << st) + (u >> (LOGR - st));
+            gs_bfly(x[v], x[v + dist], w[idx], q);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < E; v++) s[PAD(tau * E + v)] = x[v];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < E; v++) x[v] = s[PAD(tau + T * v)];
+#pragma unroll
+    for (int st = LOGE - 1; st >= 0; st--) {
+        const int half = E >> (st + 1);
+#pragma unroll
+        for (int v = 0; v < E; v++) {
+            if (v & half) continue;
+            const size_t idx = (size_t(1) << (k1 + st)) + (h << st) + (v >> (LOGE - st));
+            gs_bfly(x[v], x[v + half], w[idx], q);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < E; v++) out[h * R + tau + T * v] = x[v];
+#undef PAD
+}
+
+template <int LOGR, int LOGE>
+__global__ void __launch_bounds__(256)
+k_ntt_inv_cols(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__restrict__ mods,
+               const ulonglong2 *__restrict__ tw, int log_n) {
+    constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CW = 256 / T;
+    __shared__ uint64_t sm[R * CW];
+    const uint32_t limb = blockIdx.y;
+    const uint32_t g = limb / map.period, r = limb % map.period;
+    const size_t N = size_t(1) << log_n;
+    const size_t S = N >> LOGR;
+    uint64_t *out = data + (size_t(g) * map.dst_stride + map.dst_off[r]) * N;
+    const int p = map.prime[r];
+    const DevMod m = mods[p];
+    const uint64_t q = m.q;
+    const ulonglong2 *w = tw + size_t(p) * N;
+    const int cl = threadIdx.x % CW, tau = threadIdx.x / CW;
+    const size_t c = size_t(blockIdx.x) * CW + cl;
+
+    uint64_t x[E];
+#pragma unroll
+    for (int v = 0; v < E; v++) x[v] = out[c + size_t(tau * E + v) * S];
+#pragma unroll
+    for (int st = LOGR - 1; st >= LOGE; st--) {
+        const int dist = 1 << (LOGR - 1 - st);
+#pragma unroll
+        for (int v = 0; v < E; v++) {
+            if (v & dist) continue;
+            const int rr = tau * E + v;
+            gs_bfly(x[v], x[v + dist], w[(1 << st) + (rr >> (LOGR - st))], q);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < E; v++) sm[(tau * E + v) * CW + cl] = x[v];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < E; v++) x[v] = sm[(tau + T * v) * CW + cl];
+#pragma unroll
+    for (int st = LOGE - 1; st >= 1; st--) {
+        const int half = E >> (st + 1);
+#pragma unroll
+        for (int v = 0; v < E; v++) {
+            if (v & half) continue;
+            gs_bfly(x[v], x[v + half], w[(1 << st) + (v >> (LOGE - st))], q);
+        }
+    }
+    // stage 0 with N^-1 folded in: (a + b) N^-1, (a - b) psi^-bitrev(1) N^-1
+    {
+        constexpr int half = E / 2;
+#pragma unroll
+        for (int v = 0; v < half; v++) {
+            const uint64_t a0 = x[v], b0 = x[v + half];
+            x[v] = shoup(a0 + b0, m.ninv, m.ninv_s, q);
+            x[v + half] = shoup(a0 + q - b0, m.ninvw, m.ninvw_s, q);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < E; v++) out[c + size_t(tau + T * v) * S] = x[v];
+}
+
+// ------------------------------------------------------------------ launchers
+
+template <int R1, int E1, int R2, int E2>
+static int run_fwd(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
+                   uint32_t n_limbs, cudaStream_t s) {
+    const size_t N = c.n;
+    dim3 g1(unsigned((N >> R1) / (256 / ((1 << R1) >> E1))), n_limbs);
+    k_ntt_fwd_cols<R1, E1><<<g1, 256, 0, s>>>(src, dst, map, c.d_mods, c.d_twf, c.log_n);
+    dim3 g2(unsigned((N >> R2) / (256 / ((1 << R2) >> E2))), n_limbs);
+    k_ntt_fwd_rows<R2, E2><<<g2, 256, 0, s>>>(dst, map, c.d_mods, c.d_twf, c.log_n);
+    return cudaGetLastError() == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
+}
+
+template <int R1, int E1, int R2, int E2>
+static int run_inv(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
+                   uint32_t n_limbs, cudaStream_t s) {
+    const size_t N = c.n;
+    dim3 g2(unsigned((N >> R2) / (256 / ((1 << R2) >> E2))), n_limbs);
+    k_ntt_inv_rows<R2, E2><<<g2, 256, 0, s>>>(src, dst, map, c.d_mods, c.d_twi, c.log_n);
+    dim3 g1(unsigned((N >> R1) / (256 / ((1 << R1) >> E1))), n_limbs);
+    k_ntt_inv_cols<R1, E1><<<g1, 256, 0, s>>>(dst, map, c.d_mods, c.d_twi, c.log_n);
+    return cudaGetLastError() == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
+}
+
+// (column pass log size, its LOGE, row pass log size, its LOGE) per log N
+int launch_ntt_fwd(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
+                   uint32_t n_limbs, cudaStream_t s) {
+    if (n_limbs == 0) return CATFHE_OK;
+    switch (c.log_n) {
+        case 12: return run_fwd<6, 3, 6, 3>(c, src, dst, map, n_limbs, s);
+        case 13: return run_fwd<7, 4, 6, 3>(c, src, dst, map, n_limbs, s);
+        case 14: return run_fwd<7, 4, 7, 4>(c, src, dst, map, n_limbs, s);
+        case 15: return run_fwd<8, 4, 7, 4>(c, src, dst, map, n_limbs, s);
+        case 16: return run_fwd<8, 4, 8, 4>(c, src, dst, map, n_limbs, s);
+        default: return CATFHE_EINVAL;
+    }
+}
+
+int launch_ntt_inv(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
+                   uint32_t n_limbs, cudaStream_t s) {
+    if (n_limbs == 0) return CATFHE_OK;
+    switch (c.log_n) {
+        case 12: return run_inv<6, 3, 6, 3>(c, src, dst, map, n_limbs, s);
+        case 13: return run_inv<7, 4, 6, 3>(c, src, dst, map, n_limbs, s);
+        case 14: return run_inv<7, 4, 7, 4>(c, src, dst, map, n_limbs, s);
+        case 15: return run_inv<8, 4, 7, 4>(c, src, dst, map, n_limbs, s);
+        case 16: return run_inv<8, 4, 8, 4>(c, src, dst, map, n_limbs, s);
+        default: return CATFHE_EINVAL;
+    }
+}
+
+}  // namespace catfhe

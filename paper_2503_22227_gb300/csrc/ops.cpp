@@ -1,0 +1,1004 @@
+// Scheme operations: key generation, encryption, decryption, and the hot
+// path (tensor -> ModUp -> inner product -> ModDown [-> rescale]), as
+// sequences of batched kernel launches on one stream.
+//
+// Every step follows the definitions the CPU oracle computes (hybrid key
+// switching with exact centred lifts; ModDown round(x / P), or
+// (x - t [x t^-1]_P) / P for BGV; CKKS rescale round(c / q_{l-1}); BFV
+// multiplication by exact round(t x / Q) over an auxiliary basis).
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "internal.h"
+
+namespace catfhe {
+
+const uint64_t *get_plan(Context &c, const std::string &key, const PlanSpec &spec,
+                         uint32_t *words);
+const uint64_t *get_plan_extra(Context &c, const std::string &key, const PlanSpec &spec,
+                               const std::vector<uint64_t> &extra, uint32_t *words);
+
+#define TRY(x)                      \
+    do {                            \
+        int rc_ = (x);              \
+        if (rc_ != CATFHE_OK) return rc_; \
+    } while (0)
+
+// ----------------------------------------------------------------- workspace
+
+struct Bump {
+    char *base;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+static int get_ws(Context &c, void *ws, size_t ws_bytes, size_t need, char **out) {
+    if (ws) {
+        if (ws_bytes < need) return CATFHE_EWORKSPACE;
+        *out = static_cast<char *>(ws);
+        return CATFHE_OK;
+    }
+    if (c.scratch.bytes < need) {
+        cudaFree(c.scratch.ptr);
+        c.scratch.ptr = nullptr;
+        c.scratch.bytes = 0;
+        if (cudaMalloc(&c.scratch.ptr, need) != cudaSuccess) return CATFHE_ENOMEM;
+        c.scratch.bytes = need;
+    }
+    *out = static_cast<char *>(c.scratch.ptr);
+    return CATFHE_OK;
+}
+
+static LimbMap map_identity(uint32_t limbs, uint32_t first_prime = 0) {
+    LimbMap m{};
+    m.period = limbs;
+    m.src_stride = m.dst_stride = limbs;
+    for (uint32_t i = 0; i < limbs; i++) {
+        m.src_off[i] = m.dst_off[i] = uint16_t(i);
+        m.prime[i] = uint8_t(first_prime + i);
+    }
+    return m;
+}
+
+static uint64_t prod_mod(const Context &c, int from, int to, uint64_t m) {
+    uint64_t r = 1 % m;
+    for (int i = from; i < to; i++) r = h_mulmod(r, c.mod(i) % m, m);
+    return r;
+}
+
+// P = prod p_k mod m
+static uint64_t pmod(const Context &c, uint64_t m) { return prod_mod(c, c.L, c.L + c.K, m); }
+
+// ----------------------------------------------------------------- key switching pieces
+
+// Global prime index of extended position i at level l (Q_l then P).
+static int ext_prime(const Context &c, int level, int i) { return i < level ? i : c.L + (i - level); }
+
+// ModUp: lift each digit of d2 (coefficient form, [count][level][N]) to the
+// other primes of Q_l u P, written into ext ([count][beta][M][N]).
+static int modup(Context &c, const uint64_t *d2c, uint64_t *ext, uint32_t count, int level,
+                 bool own_too, cudaStream_t s) {
+    const int M = level + c.K, beta = (level + c.alpha - 1) / c.alpha;
+    PlanList pl{};
+    pl.n = beta;
+    for (int j = 0; j < beta; j++) {
+        const int lo = j * c.alpha, hi = std::min((j + 1) * c.alpha, level);
+        PlanSpec sp;
+        for (int i = lo; i < hi; i++) {
+            sp.src_mod.push_back(c.mod(i));
+            sp.src_off.push_back(uint32_t(i));
+        }
+        for (int i = 0; i < M; i++) {
+            if (!own_too && i >= lo && i < hi) continue;
+            sp.dst_mod.push_back(c.mod(ext_prime(c, level, i)));
+            sp.dst_off.push_back(uint32_t(i));
+        }
+        uint32_t w = 0;
+        const std::string key = "modup/" + std::to_string(level) + "/" + std::to_string(j) +
+                                (own_too ? "/own" : "");
+        pl.p[j] = get_plan(c, key, sp, &w);
+        if (!pl.p[j]) return CATFHE_ENOMEM;
+        pl.kmax = std::max<uint32_t>(pl.kmax, uint32_t(hi - lo));
+        pl.words = std::max(pl.words, w);
+    }
+    const size_t n = c.n;
+    return launch_conv(c, pl, d2c, size_t(level) * n, 0, ext, size_t(beta) * M * n, size_t(M) * n,
+                       count, s);
+}
+
+// NTT of the lifted limbs of ext (all positions if own_too).
+static int ntt_ext(Context &c, uint64_t *ext, uint32_t count, int level, bool own_too,
+                   cudaStream_t s) {
+    const int M = level + c.K, beta = (level + c.alpha - 1) / c.alpha;
+    LimbMap m{};
+    uint32_t e = 0;
+    for (int j = 0; j < beta; j++) {
+        const int lo = j * c.alpha, hi = std::min((j + 1) * c.alpha, level);
+        for (int i = 0; i < M; i++) {
+            if (!own_too && i >= lo && i < hi) continue;
+            if (e >= uint32_t(kMapMax)) return CATFHE_EINVAL;
+            m.src_off[e] = m.dst_off[e] = uint16_t(j * M + i);
+            m.prime[e] = uint8_t(ext_prime(c, level, i));
+            e++;
+        }
+    }
+    m.period = e;
+    m.src_stride = m.dst_stride = uint32_t(beta * M);
+    return launch_ntt_fwd(c, ext, ext, m, e * count, s);
+}
+
+static int inner_product(Context &c, const uint64_t *ext, const uint64_t *own, const uint64_t *key,
+                         const uint64_t *add0, const uint64_t *add1, uint64_t *y, uint32_t count,
+                         int level, cudaStream_t s) {
+    const int M = level + c.K, beta = (level + c.alpha - 1) / c.alpha;
+    const size_t n = c.n;
+    IpArgs a{};
+    a.ext = ext;
+    a.own = own;
+    a.key = key;
+    a.add0 = add0;
+    a.add1 = add1;
+    a.y = y;
+    a.ext_item = size_t(beta) * M * n;
+    a.own_item = size_t(level) * n;
+    a.add_item = size_t(level) * n;
+    a.y_item = size_t(2) * M * n;
+    a.M = M;
+    a.level = level;
+    a.beta = beta;
+    a.L = c.L;
+    a.K = c.K;
+    a.alpha = c.alpha;
+    for (int i = 0; i < M; i++) {
+        const int gp = ext_prime(c, level, i);
+        a.prime[i] = uint8_t(gp);
+        a.key_limb[i] = uint16_t(gp);
+        if (i < level) {
+            a.pfac[i] = pmod(c, c.mod(i));
+            a.pfac_s[i] = h_shoup(a.pfac[i], c.mod(i));
+        }
+    }
+    return launch_ip(c, a, count, s);
+}
+
+// ModDown of y ([count][2][M][N]; NTT form for CKKS/BGV, coefficient form
+// for BFV) by D = P (fused: P q_{l-1}) into out ([count][2][lo][N]).
+static int moddown(Context &c, uint64_t *y, uint64_t *lift, uint64_t *out, const uint64_t *add,
+                   uint32_t count, int level, bool fused, cudaStream_t s) {
+    const int M = level + c.K, lo = fused ? level - 1 : level;
+    const size_t n = c.n;
+    const bool ntt_form = c.scheme != CATFHE_BFV;
+    // division basis positions in y: P, then q_{l-1} when fused
+    std::vector<int> dpos;
+    for (int k = 0; k < c.K; k++) dpos.push_back(level + k);
+    if (fused) dpos.push_back(level - 1);
+    const int Kd = int(dpos.size());
+    if (ntt_form) {
+        LimbMap m{};
+        m.period = uint32_t(2 * Kd);
+        m.src_stride = m.dst_stride = uint32_t(2 * M);
+        for (int p = 0; p < 2; p++)
+            for (int d = 0; d < Kd; d++) {
+                m.src_off[p * Kd + d] = m.dst_off[p * Kd + d] = uint16_t(p * M + dpos[d]);
+                m.prime[p * Kd + d] = uint8_t(ext_prime(c, level, dpos[d]));
+            }
+        TRY(launch_ntt_inv(c, y, y, m, m.period * count, s));
+    }
+    PlanSpec sp;
+    for (int d = 0; d < Kd; d++) {
+        sp.src_mod.push_back(c.mod(ext_prime(c, level, dpos[d])));
+        sp.src_off.push_back(uint32_t(dpos[d]));
+    }
+    for (int i = 0; i < lo; i++) {
+        sp.dst_mod.push_back(c.mod(i));
+        sp.dst_off.push_back(uint32_t(i));
+    }
+    if (c.scheme == CATFHE_BGV) {
+        for (int d = 0; d < Kd; d++) sp.pre.push_back(h_invmod(c.t % sp.src_mod[d], sp.src_mod[d]));
+        for (int i = 0; i < lo; i++) sp.post.push_back(c.t % c.mod(i));
+    }
+    uint32_t w = 0;
+    PlanList pl{};
+    pl.n = 1;
+    pl.kmax = uint32_t(Kd);
+    pl.p[0] = get_plan(c, "moddown/" + std::to_string(level) + (fused ? "/f" : ""), sp, &w);
+    if (!pl.p[0]) return CATFHE_ENOMEM;
+    pl.words = w;
+    TRY(launch_conv(c, pl, y, size_t(M) * n, 0, lift, size_t(lo) * n, 0, 2 * count, s));
+    if (ntt_form) {
+        LimbMap m = map_identity(uint32_t(lo));
+        TRY(launch_ntt_fwd(c, lift, lift, m, uint32_t(2 * lo) * count, s));
+    }
+    CombineArgs a{};
+    a.y = y;
+    a.lift = lift;
+    a.add = add;
+    a.out = out;
+    a.y_item = size_t(2) * M * n;
+    a.y_poly = size_t(M) * n;
+    a.lift_item = size_t(2) * lo * n;
+    a.lift_poly = size_t(lo) * n;
+    a.add_item = size_t(2) * lo * n;
+    a.add_poly = size_t(lo) * n;
+    a.out_item = size_t(2) * lo * n;
+    a.out_poly = size_t(lo) * n;
+    a.lo = uint32_t(lo);
+    for (int i = 0; i < lo; i++) {
+        const uint64_t q = c.mod(i);
+        uint64_t D = pmod(c, q);
+        if (fused) D = h_mulmod(D, c.mod(level - 1) % q, q);
+        a.prime[i] = uint8_t(i);
+        a.dinv[i] = h_invmod(D, q);
+        a.dinv_s[i] = h_shoup(a.dinv[i], q);
+    }
+    return launch_combine(c, a, count, s);
+}
+
+// ----------------------------------------------------------------- op layouts
+
+struct KsBufs {
+    uint64_t *d0, *d1, *d2, *d2c, *ext, *y, *lift;
+    // BFV
+    uint64_t *xin, *tens, *dq, *add;
+};
+
+static void ks_layout(const Context &c, Bump &b, KsBufs &k, uint32_t count, int level,
+                      bool fused) {
+    const size_t n = c.n;
+    const int M = level + c.K, beta = (level + c.alpha - 1) / c.alpha;
+    const int lo = fused ? level - 1 : level;
+    k.d0 = b.take<uint64_t>(size_t(count) * level * n);
+    k.d1 = b.take<uint64_t>(size_t(count) * level * n);
+    k.d2 = b.take<uint64_t>(size_t(count) * level * n);
+    k.d2c = b.take<uint64_t>(size_t(count) * level * n);
+    k.ext = b.take<uint64_t>(size_t(count) * beta * M * n);
+    k.y = b.take<uint64_t>(size_t(count) * 2 * M * n);
+    k.lift = b.take<uint64_t>(size_t(count) * 2 * lo * n);
+    k.xin = k.tens = k.dq = k.add = nullptr;
+    if (c.scheme == CATFHE_BFV) {
+        const int kb = level + c.nb;
+        k.xin = b.take<uint64_t>(size_t(count) * 4 * kb * n);
+        k.tens = b.take<uint64_t>(size_t(count) * 3 * kb * n);
+        k.dq = b.take<uint64_t>(size_t(count) * 3 * level * n);
+        k.add = b.take<uint64_t>(size_t(count) * 2 * level * n);
+    }
+}
+
+size_t ws_bytes(const Context &c, int op, uint32_t level, uint32_t count) {
+    Bump b{nullptr};
+    KsBufs k{};
+    const size_t n = c.n;
+    switch (op) {
+        case CATFHE_OP_MUL_RELIN:
+        case CATFHE_OP_ROTATE:
+            ks_layout(c, b, k, count, int(level), false);
+            break;
+        case CATFHE_OP_MUL_RELIN_RESCALE:
+            ks_layout(c, b, k, count, int(level), true);
+            break;
+        case CATFHE_OP_RESCALE:
+            b.take<uint64_t>(size_t(count) * 2 * n);
+            b.take<uint64_t>(size_t(count) * 2 * (level ? level - 1 : 0) * n);
+            break;
+        case CATFHE_OP_DECRYPT:
+            b.take<uint64_t>(size_t(level) * n);
+            b.take<uint64_t>(size_t(level) * n);
+            b.take<int64_t>(n);
+            break;
+        case CATFHE_OP_EXPORT:
+            b.take<uint64_t>(size_t(count) * 2 * level * n);
+            break;
+        default:
+            return 0;
+    }
+    return b.off + 256;
+}
+
+// ----------------------------------------------------------------- hot path
+
+static int key_for(const Keys &k, uint64_t id, const uint64_t **key) {
+    auto it = k.ksk.find(id);
+    if (it == k.ksk.end()) return CATFHE_ENOKEY;
+    *key = it->second;
+    return CATFHE_OK;
+}
+
+// CKKS / BGV: tensor in NTT form, INTT d2, ModUp, NTT, inner product with
+// P*(d0, d1) folded in, ModDown (fused: by P q_{l-1}).
+static int mul_relin_ntt(Context &c, const Keys &keys, const uint64_t *a, const uint64_t *b,
+                         uint64_t *out, uint32_t count, int level, bool fused, KsBufs &k,
+                         cudaStream_t s) {
+    const uint64_t *rlk;
+    TRY(key_for(keys, 0, &rlk));
+    const size_t n = c.n;
+    TensorArgs t{};
+    t.a = a;
+    t.b = b;
+    t.d0 = k.d0;
+    t.d1 = k.d1;
+    t.d2 = k.d2;
+    t.in_item = size_t(2) * level * n;
+    t.out_item = size_t(level) * n;
+    t.limbs = uint32_t(level);
+    for (int i = 0; i < level; i++) t.prime[i] = uint8_t(i);
+    TRY(launch_tensor(c, t, count, s));
+    LimbMap m = map_identity(uint32_t(level));
+    TRY(launch_ntt_inv(c, k.d2, k.d2c, m, uint32_t(level) * count, s));
+    TRY(modup(c, k.d2c, k.ext, count, level, false, s));
+    TRY(ntt_ext(c, k.ext, count, level, false, s));
+    TRY(inner_product(c, k.ext, k.d2, rlk, k.d0, k.d1, k.y, count, level, s));
+    return moddown(c, k.y, k.lift, out, nullptr, count, level, fused, s);
+}
+
+// BFV: lift to Q u B, NTT, tensor, INTT, exact round(t x / Q) back to Q,
+// then relinearise d2 in coefficient form.
+static int mul_relin_bfv(Context &c, const Keys &keys, const uint64_t *a, const uint64_t *b,
+                         uint64_t *out, uint32_t count, int level, KsBufs &k, cudaStream_t s) {
+    const uint64_t *rlk;
+    TRY(key_for(keys, 0, &rlk));
+    const size_t n = c.n;
+    const int kb = level + c.nb;
+    // 1. centred lift of the 4 input polys from Q_l to Q_l u B
+    {
+        PlanSpec sp;
+        for (int i = 0; i < level; i++) {
+            sp.src_mod.push_back(c.mod(i));
+            sp.src_off.push_back(uint32_t(i));
+        }
+        for (int i = 0; i < kb; i++) {
+            sp.dst_mod.push_back(c.mod(i < level ? i : c.pb(i - level)));
+            sp.dst_off.push_back(uint32_t(i));
+        }
+        uint32_t w = 0;
+        PlanList pl{};
+        pl.n = 1;
+        pl.kmax = uint32_t(level);
+        pl.p[0] = get_plan(c, "bfv_lift/" + std::to_string(level), sp, &w);
+        if (!pl.p[0]) return CATFHE_ENOMEM;
+        pl.words = w;
+        // items: (ct, poly) for a then for b
+        TRY(launch_conv(c, pl, a, size_t(level) * n, 0, k.xin, size_t(kb) * n, 0, 2 * count, s));
+        TRY(launch_conv(c, pl, b, size_t(level) * n, 0, k.xin + size_t(count) * 2 * kb * n,
+                        size_t(kb) * n, 0, 2 * count, s));
+    }
+    LimbMap mq{};
+    mq.period = uint32_t(kb);
+    mq.src_stride = mq.dst_stride = uint32_t(kb);
+    for (int i = 0; i < kb; i++) {
+        mq.src_off[i] = mq.dst_off[i] = uint16_t(i);
+        mq.prime[i] = uint8_t(i < level ? i : c.pb(i - level));
+    }
+    TRY(launch_ntt_fwd(c, k.xin, k.xin, mq, uint32_t(kb) * 4 * count, s));
+    // 2. tensor over Q u B
+    {
+        TensorArgs t{};
+        t.a = k.xin;
+        t.b = k.xin + size_t(count) * 2 * kb * n;
+        t.in_item = size_t(2) * kb * n;
+        t.d0 = k.tens;
+        t.d1 = k.tens + size_t(kb) * n;
+        t.d2 = k.tens + size_t(2) * kb * n;
+        t.out_item = size_t(3) * kb * n;
+        t.limbs = uint32_t(kb);
+        for (int i = 0; i < kb; i++) t.prime[i] = mq.prime[i];
+        TRY(launch_tensor(c, t, count, s));
+    }
+    TRY(launch_ntt_inv(c, k.tens, k.tens, mq, uint32_t(kb) * 3 * count, s));
+    // 3. exact round(t x / Q) back to Q_l
+    {
+        PlanSpec A, B;
+        std::vector<uint64_t> tq;
+        for (int i = 0; i < level; i++) {
+            A.src_mod.push_back(c.mod(i));
+            A.src_off.push_back(uint32_t(i));
+            A.pre.push_back(c.t % c.mod(i));
+        }
+        for (int j = 0; j < c.nb; j++) {
+            const uint64_t bj = c.mod(c.pb(j));
+            const uint64_t qinv = h_invmod(prod_mod(c, 0, level, bj), bj);
+            A.dst_mod.push_back(bj);
+            A.dst_off.push_back(uint32_t(level + j));
+            A.post.push_back(qinv);
+            const uint64_t tqi = h_mulmod(c.t % bj, qinv, bj);
+            tq.push_back(tqi);
+            tq.push_back(h_shoup(tqi, bj));
+            B.src_mod.push_back(bj);
+            B.src_off.push_back(0);
+        }
+        for (int i = 0; i < level; i++) {
+            B.dst_mod.push_back(c.mod(i));
+            B.dst_off.push_back(uint32_t(i));
+        }
+        uint32_t wa = 0, wb = 0;
+        const uint64_t *pa = get_plan_extra(c, "bfv_sr_a/" + std::to_string(level), A, tq, &wa);
+        const uint64_t *pb = get_plan(c, "bfv_sr_b/" + std::to_string(level), B, &wb);
+        if (!pa || !pb) return CATFHE_ENOMEM;
+        TRY(launch_bfv_scale_round(c, pa, wa, pb, wb, k.tens, size_t(kb) * n, k.dq,
+                                   size_t(level) * n, 3 * count, s));
+    }
+    // 4. relinearise d2' (coefficient form) and add (d0', d1')
+    const uint64_t *d2 = k.dq + size_t(2) * level * n;
+    // ModUp reads the digit limbs of d2' per ct: item stride 3*level*N
+    {
+        const int M = level + c.K, beta = (level + c.alpha - 1) / c.alpha;
+        PlanList pl{};
+        pl.n = beta;
+        for (int j = 0; j < beta; j++) {
+            const int lo = j * c.alpha, hi = std::min((j + 1) * c.alpha, level);
+            PlanSpec sp;
+            for (int i = lo; i < hi; i++) {
+                sp.src_mod.push_back(c.mod(i));
+                sp.src_off.push_back(uint32_t(i));
+            }
+            for (int i = 0; i < M; i++) {
+                sp.dst_mod.push_back(c.mod(ext_prime(c, level, i)));
+                sp.dst_off.push_back(uint32_t(i));
+            }
+            uint32_t w = 0;
+            pl.p[j] = get_plan(c, "modup/" + std::to_string(level) + "/" + std::to_string(j) + "/own",
+                               sp, &w);
+            if (!pl.p[j]) return CATFHE_ENOMEM;
+            pl.kmax = std::max<uint32_t>(pl.kmax, uint32_t(hi - lo));
+            pl.words = std::max(pl.words, w);
+        }
+        TRY(launch_conv(c, pl, d2, size_t(3) * level * n, 0, k.ext, size_t(beta) * M * n,
+                        size_t(M) * n, count, s));
+    }
+    TRY(ntt_ext(c, k.ext, count, level, true, s));
+    TRY(inner_product(c, k.ext, nullptr, rlk, nullptr, nullptr, k.y, count, level, s));
+    {
+        const int M = level + c.K;
+        LimbMap my = map_identity(uint32_t(M));
+        for (int i = 0; i < M; i++) my.prime[i] = uint8_t(ext_prime(c, level, i));
+        TRY(launch_ntt_inv(c, k.y, k.y, my, uint32_t(2 * M) * count, s));
+    }
+    // (d0', d1') of [count][3][level] packed as [count][2][level] for the combine
+    {
+        LimbMap cp{};
+        cp.period = uint32_t(2 * level);
+        cp.src_stride = uint32_t(3 * level);
+        cp.dst_stride = uint32_t(2 * level);
+        for (int i = 0; i < 2 * level; i++) {
+            cp.src_off[i] = cp.dst_off[i] = uint16_t(i);
+            cp.prime[i] = uint8_t(i % level);
+        }
+        TRY(launch_copy_limbs(c, k.dq, k.add, cp, uint32_t(2 * level) * count, s));
+    }
+    return moddown(c, k.y, k.lift, out, k.add, count, level, false, s);
+}
+
+int op_mul_relin(Context &c, const Keys &keys, const uint64_t *a, const uint64_t *b,
+                 uint64_t *out, uint32_t level, uint32_t count, bool fused, void *ws,
+                 size_t ws_bytes_in, cudaStream_t s) {
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    if (fused && (c.scheme != CATFHE_CKKS)) return CATFHE_ESCHEME;
+    if (fused && level < 2) return CATFHE_ELEVEL;
+    if (count == 0) return CATFHE_OK;
+    const size_t need = ws_bytes(c, fused ? CATFHE_OP_MUL_RELIN_RESCALE : CATFHE_OP_MUL_RELIN,
+                                 level, count);
+    char *base;
+    TRY(get_ws(c, ws, ws_bytes_in, need, &base));
+    Bump bump{base};
+    KsBufs k{};
+    ks_layout(c, bump, k, count, int(level), fused);
+    if (c.scheme == CATFHE_BFV) return mul_relin_bfv(c, keys, a, b, out, count, int(level), k, s);
+    return mul_relin_ntt(c, keys, a, b, out, count, int(level), fused, k, s);
+}
+
+int op_rotate(Context &c, const Keys &keys, const uint64_t *a, uint64_t g, uint64_t *out,
+              uint32_t level, uint32_t count, void *ws, size_t ws_bytes_in, cudaStream_t s) {
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    g %= 2 * c.n;
+    if (!(g & 1)) return CATFHE_EINVAL;
+    const uint64_t *gk;
+    TRY(key_for(keys, g, &gk));
+    if (count == 0) return CATFHE_OK;
+    char *base;
+    TRY(get_ws(c, ws, ws_bytes_in, ws_bytes(c, CATFHE_OP_ROTATE, level, count), &base));
+    Bump bump{base};
+    KsBufs k{};
+    ks_layout(c, bump, k, count, int(level), false);
+    const size_t n = c.n;
+    const int lvl = int(level);
+    if (c.scheme != CATFHE_BFV) {
+        // sigma_g on both components in NTT form: d0 <- sigma(c0), d2 <- sigma(c1)
+        for (uint32_t ct = 0; ct < count; ct++) {
+            const uint64_t *src = a + size_t(ct) * 2 * lvl * n;
+            TRY(launch_automorph_ntt(c, src, k.d0 + size_t(ct) * lvl * n, uint32_t(lvl), g, s));
+            TRY(launch_automorph_ntt(c, src + size_t(lvl) * n, k.d2 + size_t(ct) * lvl * n,
+                                     uint32_t(lvl), g, s));
+        }
+        LimbMap m = map_identity(uint32_t(lvl));
+        TRY(launch_ntt_inv(c, k.d2, k.d2c, m, uint32_t(lvl) * count, s));
+        TRY(modup(c, k.d2c, k.ext, count, lvl, false, s));
+        TRY(ntt_ext(c, k.ext, count, lvl, false, s));
+        TRY(inner_product(c, k.ext, k.d2, gk, k.d0, nullptr, k.y, count, lvl, s));
+        return moddown(c, k.y, k.lift, out, nullptr, count, lvl, false, s);
+    }
+    // BFV (coefficient form): (sigma(c0), 0) becomes the added pair of the
+    // ModDown combine, sigma(c1) is key switched.
+    uint64_t *addbuf = k.add;  // [count][2][level]
+    {
+        LimbMap m{};
+        m.period = uint32_t(lvl);
+        m.src_stride = uint32_t(2 * lvl);
+        m.dst_stride = uint32_t(2 * lvl);
+        for (int i = 0; i < lvl; i++) {
+            m.src_off[i] = m.dst_off[i] = uint16_t(i);
+            m.prime[i] = uint8_t(i);
+        }
+        TRY(launch_automorph_coeff(c, a, addbuf, m, uint32_t(lvl) * count, g, s));
+        for (uint32_t ct = 0; ct < count; ct++)
+            if (cudaMemsetAsync(addbuf + (size_t(ct) * 2 + 1) * lvl * n, 0, size_t(lvl) * n * 8, s) !=
+                cudaSuccess)
+                return CATFHE_ECUDA;
+        LimbMap m1 = m;
+        m1.dst_stride = uint32_t(lvl);
+        for (int i = 0; i < lvl; i++) m1.src_off[i] = uint16_t(lvl + i);
+        TRY(launch_automorph_coeff(c, a, k.d2c, m1, uint32_t(lvl) * count, g, s));
+    }
+    TRY(modup(c, k.d2c, k.ext, count, lvl, true, s));
+    TRY(ntt_ext(c, k.ext, count, lvl, true, s));
+    TRY(inner_product(c, k.ext, nullptr, gk, nullptr, nullptr, k.y, count, lvl, s));
+    {
+        const int M = lvl + c.K;
+        LimbMap my = map_identity(uint32_t(M));
+        for (int i = 0; i < M; i++) my.prime[i] = uint8_t(ext_prime(c, lvl, i));
+        TRY(launch_ntt_inv(c, k.y, k.y, my, uint32_t(2 * M) * count, s));
+    }
+    return moddown(c, k.y, k.lift, out, addbuf, count, lvl, false, s);
+}
+
+// CKKS rescale / BGV modulus switch: divide by q_{l-1}.
+int op_rescale(Context &c, const uint64_t *a, uint64_t *out, uint32_t level, uint32_t count,
+               void *ws, size_t ws_bytes_in, cudaStream_t s) {
+    if (c.scheme == CATFHE_BFV) return CATFHE_ESCHEME;
+    if (level < 2 || int(level) > c.L) return CATFHE_ELEVEL;
+    if (count == 0) return CATFHE_OK;
+    char *base;
+    TRY(get_ws(c, ws, ws_bytes_in, ws_bytes(c, CATFHE_OP_RESCALE, level, count), &base));
+    Bump bump{base};
+    const size_t n = c.n;
+    const int lvl = int(level), lo = lvl - 1;
+    uint64_t *last = bump.take<uint64_t>(size_t(count) * 2 * n);
+    uint64_t *lift = bump.take<uint64_t>(size_t(count) * 2 * lo * n);
+    // INTT of the last limb of both polys: [count][2][level] -> [count][2][1]
+    LimbMap m{};
+    m.period = 2;
+    m.src_stride = uint32_t(2 * lvl);
+    m.dst_stride = 2;
+    for (int p = 0; p < 2; p++) {
+        m.src_off[p] = uint16_t(p * lvl + lvl - 1);
+        m.dst_off[p] = uint16_t(p);
+        m.prime[p] = uint8_t(lvl - 1);
+    }
+    TRY(launch_ntt_inv(c, a, last, m, 2 * count, s));
+    PlanSpec sp;
+    sp.src_mod.push_back(c.mod(lvl - 1));
+    sp.src_off.push_back(0);
+    for (int i = 0; i < lo; i++) {
+        sp.dst_mod.push_back(c.mod(i));
+        sp.dst_off.push_back(uint32_t(i));
+    }
+    if (c.scheme == CATFHE_BGV) {
+        sp.pre.push_back(h_invmod(c.t % c.mod(lvl - 1), c.mod(lvl - 1)));
+        for (int i = 0; i < lo; i++) sp.post.push_back(c.t % c.mod(i));
+    }
+    uint32_t w = 0;
+    PlanList pl{};
+    pl.n = 1;
+    pl.kmax = 1;
+    pl.p[0] = get_plan(c, "rescale/" + std::to_string(lvl), sp, &w);
+    if (!pl.p[0]) return CATFHE_ENOMEM;
+    pl.words = w;
+    TRY(launch_conv(c, pl, last, n, 0, lift, size_t(lo) * n, 0, 2 * count, s));
+    LimbMap ml = map_identity(uint32_t(lo));
+    TRY(launch_ntt_fwd(c, lift, lift, ml, uint32_t(2 * lo) * count, s));
+    CombineArgs ca{};
+    ca.y = a;
+    ca.lift = lift;
+    ca.out = out;
+    ca.y_item = size_t(2) * lvl * n;
+    ca.y_poly = size_t(lvl) * n;
+    ca.lift_item = size_t(2) * lo * n;
+    ca.lift_poly = size_t(lo) * n;
+    ca.out_item = size_t(2) * lo * n;
+    ca.out_poly = size_t(lo) * n;
+    ca.lo = uint32_t(lo);
+    for (int i = 0; i < lo; i++) {
+        ca.prime[i] = uint8_t(i);
+        ca.dinv[i] = h_invmod(c.mod(lvl - 1) % c.mod(i), c.mod(i));
+        ca.dinv_s[i] = h_shoup(ca.dinv[i], c.mod(i));
+    }
+    return launch_combine(c, ca, count, s);
+}
+
+int op_add(Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t level,
+           uint32_t count, cudaStream_t s) {
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    if (count == 0) return CATFHE_OK;
+    LimbMap m{};
+    m.period = 2 * level;
+    m.src_stride = m.dst_stride = 2 * level;
+    for (uint32_t i = 0; i < 2 * level; i++) {
+        m.src_off[i] = m.dst_off[i] = uint16_t(i);
+        m.prime[i] = uint8_t(i % level);
+    }
+    return launch_add(c, a, b, out, m, 2 * level * count, s);
+}
+
+int op_ntt(Context &c, uint64_t *limbs, uint32_t level, uint32_t count, int inverse,
+           cudaStream_t s) {
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    LimbMap m = map_identity(level);
+    return inverse ? launch_ntt_inv(c, limbs, limbs, m, level * count, s)
+                   : launch_ntt_fwd(c, limbs, limbs, m, level * count, s);
+}
+
+// ----------------------------------------------------------------- keys
+
+static SampleArgs sample_args(const Context &c, const uint8_t seed[32], uint32_t tag, uint32_t i0,
+                              uint32_t i1, uint32_t kind) {
+    SampleArgs a{};
+    for (int i = 0; i < 8; i++)
+        a.key[i] = uint32_t(seed[4 * i]) | (uint32_t(seed[4 * i + 1]) << 8) |
+                   (uint32_t(seed[4 * i + 2]) << 16) | (uint32_t(seed[4 * i + 3]) << 24);
+    a.tag = tag;
+    a.i0 = i0;
+    a.i1 = i1;
+    a.kind = kind;
+    memcpy(a.cdt, c.cdt, sizeof(a.cdt));
+    return a;
+}
+
+enum { TAG_SK = 1, TAG_PK_A = 2, TAG_PK_E = 3, TAG_KSK_A = 4, TAG_KSK_E = 5, TAG_ENC_V = 6,
+       TAG_ENC_E0 = 7, TAG_ENC_E1 = 8, TAG_CT_UNIFORM = 9 };
+
+// Device array of t mod prime (Shoup pairs) for BGV error scaling.
+struct DevConst {
+    uint64_t *v = nullptr, *s = nullptr;
+    ~DevConst() {
+        cudaFree(v);
+        cudaFree(s);
+    }
+    int set(const std::vector<uint64_t> &vals, const std::vector<uint64_t> &mods) {
+        std::vector<uint64_t> sh(vals.size());
+        for (size_t i = 0; i < vals.size(); i++) sh[i] = h_shoup(vals[i], mods[i]);
+        if (cudaMalloc(&v, vals.size() * 8) != cudaSuccess) return CATFHE_ENOMEM;
+        if (cudaMalloc(&s, vals.size() * 8) != cudaSuccess) return CATFHE_ENOMEM;
+        if (cudaMemcpy(v, vals.data(), vals.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+            return CATFHE_ECUDA;
+        if (cudaMemcpy(s, sh.data(), vals.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+            return CATFHE_ECUDA;
+        return CATFHE_OK;
+    }
+};
+
+static int gen_ksk(Context &c, Keys &k, uint64_t id, const uint64_t *sp, cudaStream_t s) {
+    const size_t n = c.n;
+    const int E = c.L + c.K;
+    uint64_t *key = nullptr, *e = nullptr;
+    if (cudaMalloc(&key, size_t(c.beta) * 2 * E * n * 8) != cudaSuccess) return CATFHE_ENOMEM;
+    if (cudaMalloc(&e, size_t(E) * n * 8) != cudaSuccess) {
+        cudaFree(key);
+        return CATFHE_ENOMEM;
+    }
+    LimbMap m = map_identity(uint32_t(E));
+    DevConst te, pf;
+    std::vector<uint64_t> mods(E), tv(E);
+    for (int i = 0; i < E; i++) {
+        mods[i] = c.mod(i);
+        tv[i] = c.scheme == CATFHE_BGV ? c.t % mods[i] : 1;
+    }
+    int rc = te.set(tv, mods);
+    for (int j = 0; j < c.beta && rc == CATFHE_OK; j++) {
+        uint64_t *bj = key + (size_t(j) * 2 + 0) * E * n;
+        uint64_t *aj = key + (size_t(j) * 2 + 1) * E * n;
+        rc = launch_sample(c, sample_args(c, k.seed, TAG_KSK_A, uint32_t(j), uint32_t(id), kUniform), aj,
+                           m, uint32_t(E), nullptr, nullptr, s);
+        if (!rc) rc = launch_ntt_fwd(c, aj, aj, m, uint32_t(E), s);
+        if (!rc)
+            rc = launch_sample(c, sample_args(c, k.seed, TAG_KSK_E, uint32_t(j), uint32_t(id), kGaussian),
+                               e, m, uint32_t(E), c.scheme == CATFHE_BGV ? te.v : nullptr,
+                               c.scheme == CATFHE_BGV ? te.s : nullptr, s);
+        if (!rc) rc = launch_ntt_fwd(c, e, e, m, uint32_t(E), s);
+        std::vector<uint64_t> pv(E, 0);
+        for (int i = j * c.alpha; i < std::min((j + 1) * c.alpha, c.L); i++) pv[i] = pmod(c, c.mod(i));
+        DevConst pfc;
+        if (!rc) rc = pfc.set(pv, mods);
+        if (!rc) rc = launch_ksk_row(c, aj, k.s_ntt, e, sp, bj, uint32_t(E), pfc.v, pfc.s, s);
+        if (!rc) rc = cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
+    }
+    cudaFree(e);
+    if (rc) {
+        cudaFree(key);
+        return rc;
+    }
+    auto it = k.ksk.find(id);
+    if (it != k.ksk.end()) cudaFree(it->second);
+    k.ksk[id] = key;
+    return CATFHE_OK;
+}
+
+int op_keygen(Context &c, const uint8_t seed[32], Keys **out) {
+    Keys *k = new Keys();
+    memcpy(k->seed, seed, 32);
+    const size_t n = c.n;
+    const int E = c.L + c.K;
+    cudaStream_t s = 0;
+    uint64_t *a = nullptr, *e = nullptr, *sp = nullptr;
+    int rc = CATFHE_OK;
+    if (cudaMalloc(&k->s_ntt, size_t(E) * n * 8) != cudaSuccess ||
+        cudaMalloc(&k->pk, size_t(2) * c.L * n * 8) != cudaSuccess ||
+        cudaMalloc(&e, size_t(E) * n * 8) != cudaSuccess ||
+        cudaMalloc(&sp, size_t(E) * n * 8) != cudaSuccess)
+        rc = CATFHE_ENOMEM;
+    LimbMap mE = map_identity(uint32_t(E)), mL = map_identity(uint32_t(c.L));
+    if (!rc) rc = launch_sample(c, sample_args(c, seed, TAG_SK, 0, 0, kTernary), k->s_ntt, mE,
+                                uint32_t(E), nullptr, nullptr, s);
+    if (!rc) rc = launch_ntt_fwd(c, k->s_ntt, k->s_ntt, mE, uint32_t(E), s);
+    // public key over Q_L
+    a = k->pk + size_t(c.L) * n;
+    if (!rc) rc = launch_sample(c, sample_args(c, seed, TAG_PK_A, 0, 0, kUniform), a, mL,
+                                uint32_t(c.L), nullptr, nullptr, s);
+    if (!rc) rc = launch_ntt_fwd(c, a, a, mL, uint32_t(c.L), s);
+    DevConst te, zero;
+    std::vector<uint64_t> mods(c.L), tv(c.L), zv(c.L, 0);
+    for (int i = 0; i < c.L; i++) {
+        mods[i] = c.mod(i);
+        tv[i] = c.scheme == CATFHE_BGV ? c.t % mods[i] : 1;
+    }
+    if (!rc) rc = te.set(tv, mods);
+    if (!rc) rc = zero.set(zv, mods);
+    if (!rc) rc = launch_sample(c, sample_args(c, seed, TAG_PK_E, 0, 0, kGaussian), e, mL,
+                                uint32_t(c.L), c.scheme == CATFHE_BGV ? te.v : nullptr,
+                                c.scheme == CATFHE_BGV ? te.s : nullptr, s);
+    if (!rc) rc = launch_ntt_fwd(c, e, e, mL, uint32_t(c.L), s);
+    if (!rc) rc = launch_ksk_row(c, a, k->s_ntt, e, nullptr, k->pk, uint32_t(c.L), zero.v, zero.s, s);
+    // relinearisation key: s' = s^2
+    if (!rc) rc = launch_pointwise(c, k->s_ntt, k->s_ntt, sp, mE, uint32_t(E), s);
+    if (!rc) rc = cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
+    if (!rc) rc = gen_ksk(c, *k, 0, sp, s);
+    cudaFree(e);
+    cudaFree(sp);
+    if (rc) {
+        cudaFree(k->s_ntt);
+        cudaFree(k->pk);
+        for (auto &kv : k->ksk) cudaFree(kv.second);
+        delete k;
+        return rc;
+    }
+    *out = k;
+    return CATFHE_OK;
+}
+
+int op_gen_galois(Context &c, Keys &k, uint64_t g) {
+    g %= 2 * c.n;
+    if (!(g & 1)) return CATFHE_EINVAL;
+    if (k.ksk.count(g)) return CATFHE_OK;
+    const int E = c.L + c.K;
+    uint64_t *sp = nullptr;
+    if (cudaMalloc(&sp, size_t(E) * c.n * 8) != cudaSuccess) return CATFHE_ENOMEM;
+    int rc = launch_automorph_ntt(c, k.s_ntt, sp, uint32_t(E), g, 0);
+    if (!rc) rc = gen_ksk(c, k, g, sp, 0);
+    cudaFree(sp);
+    return rc;
+}
+
+void keys_free(Keys *k) {
+    if (!k) return;
+    cudaFree(k->s_ntt);
+    cudaFree(k->pk);
+    for (auto &kv : k->ksk) cudaFree(kv.second);
+    delete k;
+}
+
+// Coefficient-form copies of the keys to host memory.
+int op_keys_export(Context &c, const Keys &k, uint64_t id, int64_t *s_out, uint64_t *pk_out,
+                   uint64_t *ksk_out) {
+    const size_t n = c.n;
+    const int E = c.L + c.K;
+    size_t need = size_t(c.beta) * 2 * E * n;
+    uint64_t *tmp = nullptr;
+    if (cudaMalloc(&tmp, need * 8) != cudaSuccess) return CATFHE_ENOMEM;
+    int rc = CATFHE_OK;
+    LimbMap mE = map_identity(uint32_t(E));
+    if (s_out) {
+        rc = launch_ntt_inv(c, k.s_ntt, tmp, mE, 1, 0);  // limb q_0 only
+        std::vector<uint64_t> h(n);
+        if (!rc && cudaMemcpy(h.data(), tmp, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = CATFHE_ECUDA;
+        const uint64_t q0 = c.mod(0);
+        for (size_t j = 0; j < n && !rc; j++) s_out[j] = h[j] > q0 / 2 ? int64_t(h[j]) - int64_t(q0) : int64_t(h[j]);
+    }
+    if (!rc && pk_out) {
+        LimbMap mL = map_identity(uint32_t(c.L));
+        rc = launch_ntt_inv(c, k.pk, tmp, mL, uint32_t(2 * c.L), 0);
+        if (!rc && cudaMemcpy(pk_out, tmp, size_t(2) * c.L * n * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = CATFHE_ECUDA;
+    }
+    if (!rc && ksk_out) {
+        auto it = k.ksk.find(id);
+        if (it == k.ksk.end()) rc = CATFHE_ENOKEY;
+        if (!rc) rc = launch_ntt_inv(c, it->second, tmp, mE, uint32_t(c.beta * 2 * E), 0);
+        if (!rc && cudaMemcpy(ksk_out, tmp, need * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = CATFHE_ECUDA;
+    }
+    cudaFree(tmp);
+    return rc;
+}
+
+// ----------------------------------------------------------------- encryption
+
+int op_encrypt(Context &c, const Keys &k, const int64_t *msg, const uint8_t seed[32],
+               uint64_t *ct, cudaStream_t s) {
+    const size_t n = c.n;
+    const int L = c.L;
+    int64_t *dmsg = nullptr;
+    uint64_t *v = nullptr, *tmp = nullptr;
+    int rc = CATFHE_OK;
+    if (cudaMalloc(&dmsg, n * 8) != cudaSuccess || cudaMalloc(&v, size_t(L) * n * 8) != cudaSuccess ||
+        cudaMalloc(&tmp, size_t(2) * L * n * 8) != cudaSuccess)
+        rc = CATFHE_ENOMEM;
+    if (!rc && cudaMemcpyAsync(dmsg, msg, n * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) rc = CATFHE_ECUDA;
+    LimbMap mL = map_identity(uint32_t(L));
+    std::vector<uint64_t> mods(L), tv(L), dv(L);
+    uint64_t qmodt = 1;
+    if (c.t)
+        for (int i = 0; i < L; i++) qmodt = h_mulmod(qmodt, c.mod(i) % c.t, c.t);
+    for (int i = 0; i < L; i++) {
+        mods[i] = c.mod(i);
+        tv[i] = c.scheme == CATFHE_BGV ? c.t % mods[i] : 1;
+        // BFV Delta = floor(Q/t) = (Q - (Q mod t)) / t, mod q_i
+        dv[i] = c.scheme == CATFHE_BFV
+                    ? h_mulmod((mods[i] - qmodt % mods[i]) % mods[i], h_invmod(c.t % mods[i], mods[i]), mods[i])
+                    : 1;
+    }
+    DevConst te, dl;
+    if (!rc) rc = te.set(tv, mods);
+    if (!rc) rc = dl.set(dv, mods);
+    const bool bgv = c.scheme == CATFHE_BGV;
+    uint64_t *t0 = tmp, *t1 = tmp + size_t(L) * n;
+    if (!rc) rc = launch_sample(c, sample_args(c, seed, TAG_ENC_V, 0, 0, kTernary), v, mL, uint32_t(L),
+                                nullptr, nullptr, s);
+    if (!rc) rc = launch_ntt_fwd(c, v, v, mL, uint32_t(L), s);
+    if (!rc) rc = launch_sample(c, sample_args(c, seed, TAG_ENC_E0, 0, 0, kGaussian), t0, mL,
+                                uint32_t(L), bgv ? te.v : nullptr, bgv ? te.s : nullptr, s);
+    if (!rc) rc = launch_sample(c, sample_args(c, seed, TAG_ENC_E1, 0, 0, kGaussian), t1, mL,
+                                uint32_t(L), bgv ? te.v : nullptr, bgv ? te.s : nullptr, s);
+    if (!rc) rc = launch_small_to_rns(c, dmsg, t0, mL, uint32_t(L),
+                                      c.scheme == CATFHE_BFV ? dl.v : nullptr,
+                                      c.scheme == CATFHE_BFV ? dl.s : nullptr, 1, s);
+    uint64_t *c0 = ct, *c1 = ct + size_t(L) * n;
+    if (c.scheme != CATFHE_BFV) {
+        if (!rc) rc = launch_ntt_fwd(c, tmp, tmp, mL, uint32_t(2 * L), s);
+        if (!rc) rc = launch_mul_add(c, t0, v, k.pk, c0, uint32_t(L), 0, s);
+        if (!rc) rc = launch_mul_add(c, t1, v, k.pk + size_t(L) * n, c1, uint32_t(L), 0, s);
+    } else {
+        // v pk in NTT form, back to coefficients, plus (e0 + Delta m, e1)
+        if (!rc) rc = launch_mul_add(c, nullptr, v, k.pk, c0, uint32_t(L), 0, s);
+        if (!rc) rc = launch_mul_add(c, nullptr, v, k.pk + size_t(L) * n, c1, uint32_t(L), 0, s);
+        if (!rc) rc = launch_ntt_inv(c, ct, ct, mL, uint32_t(2 * L), s);
+        LimbMap m2{};
+        m2.period = uint32_t(2 * L);
+        m2.src_stride = m2.dst_stride = uint32_t(2 * L);
+        for (int i = 0; i < 2 * L; i++) {
+            m2.src_off[i] = m2.dst_off[i] = uint16_t(i);
+            m2.prime[i] = uint8_t(i % L);
+        }
+        if (!rc) rc = launch_add(c, ct, tmp, ct, m2, uint32_t(2 * L), s);
+    }
+    if (!rc) rc = cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
+    cudaFree(dmsg);
+    cudaFree(v);
+    cudaFree(tmp);
+    return rc;
+}
+
+int op_ct_uniform(Context &c, const uint8_t seed[32], uint32_t index, uint32_t level, uint64_t *ct,
+                  cudaStream_t s) {
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    LimbMap m = map_identity(level);
+    for (uint32_t poly = 0; poly < 2; poly++)
+        TRY(launch_sample(c, sample_args(c, seed, TAG_CT_UNIFORM, poly, index, kUniform),
+                          ct + size_t(poly) * level * c.n, m, level, nullptr, nullptr, s));
+    if (c.scheme != CATFHE_BFV) TRY(launch_ntt_fwd(c, ct, ct, m, 2 * level, s));
+    return CATFHE_OK;
+}
+
+int op_import(Context &c, const uint64_t *host, uint32_t level, uint32_t count, int form,
+              uint64_t *ct, cudaStream_t s) {
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    const size_t bytes = size_t(count) * 2 * level * c.n * 8;
+    if (cudaMemcpyAsync(ct, host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return CATFHE_ECUDA;
+    if (form == CATFHE_FORM_COEFF && c.scheme != CATFHE_BFV) {
+        LimbMap m = map_identity(level);
+        TRY(launch_ntt_fwd(c, ct, ct, m, 2 * level * count, s));
+    }
+    return cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
+}
+
+int op_export(Context &c, const uint64_t *ct, uint32_t level, uint32_t count, int form,
+              uint64_t *host, void *ws, size_t ws_bytes_in, cudaStream_t s) {
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    const size_t bytes = size_t(count) * 2 * level * c.n * 8;
+    const uint64_t *src = ct;
+    if (form == CATFHE_FORM_COEFF && c.scheme != CATFHE_BFV) {
+        char *base;
+        TRY(get_ws(c, ws, ws_bytes_in, ws_bytes(c, CATFHE_OP_EXPORT, level, count), &base));
+        Bump b{base};
+        uint64_t *tmp = b.take<uint64_t>(size_t(count) * 2 * level * c.n);
+        LimbMap m = map_identity(level);
+        TRY(launch_ntt_inv(c, ct, tmp, m, 2 * level * count, s));
+        src = tmp;
+    }
+    if (cudaMemcpyAsync(host, src, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CATFHE_ECUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
+}
+
+int op_decrypt(Context &c, const Keys &k, const uint64_t *ct, uint32_t level, uint64_t factor,
+               int64_t *msg, void *ws, size_t ws_bytes_in, cudaStream_t s) {
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    if (c.scheme == CATFHE_BGV && (factor % c.t == 0 || h_invmod(factor % c.t, c.t) == 0))
+        return CATFHE_EINVAL;
+    char *base;
+    TRY(get_ws(c, ws, ws_bytes_in, ws_bytes(c, CATFHE_OP_DECRYPT, level, 1), &base));
+    Bump b{base};
+    const size_t n = c.n;
+    uint64_t *x = b.take<uint64_t>(size_t(level) * n);
+    uint64_t *tmp = b.take<uint64_t>(size_t(level) * n);
+    int64_t *res = b.take<int64_t>(n);
+    LimbMap m = map_identity(level);
+    if (c.scheme != CATFHE_BFV) {
+        TRY(launch_mul_add(c, ct, ct + size_t(level) * n, k.s_ntt, x, level, 0, s));
+        TRY(launch_ntt_inv(c, x, x, m, level, s));
+    } else {
+        TRY(launch_ntt_fwd(c, ct + size_t(level) * n, tmp, m, level, s));
+        TRY(launch_mul_add(c, nullptr, tmp, k.s_ntt, tmp, level, 0, s));
+        TRY(launch_ntt_inv(c, tmp, tmp, m, level, s));
+        TRY(launch_add(c, ct, tmp, x, m, level, s));
+    }
+    PlanSpec sp;
+    for (uint32_t i = 0; i < level; i++) {
+        sp.src_mod.push_back(c.mod(int(i)));
+        sp.src_off.push_back(i);
+    }
+    sp.dst_off.push_back(0);
+    std::string key = "decrypt/" + std::to_string(level);
+    if (c.scheme == CATFHE_CKKS) {
+        sp.dst_mod.push_back(0);
+    } else {
+        sp.dst_mod.push_back(c.t);
+        if (c.scheme == CATFHE_BFV) {
+            // round(t x / Q) mod t = -[t x]_Q Q^-1 mod t
+            for (uint32_t i = 0; i < level; i++) sp.pre.push_back(c.t % c.mod(int(i)));
+            const uint64_t qt = prod_mod(c, 0, int(level), c.t);
+            sp.post.push_back((c.t - h_invmod(qt, c.t)) % c.t);
+        }
+    }
+    uint32_t w = 0;
+    PlanList pl{};
+    pl.n = 1;
+    pl.kmax = level;
+    pl.p[0] = get_plan(c, key, sp, &w);
+    if (!pl.p[0]) return CATFHE_ENOMEM;
+    pl.words = w;
+    TRY(launch_conv(c, pl, x, 0, 0, reinterpret_cast<uint64_t *>(res), 0, 0, 1, s));
+    if (cudaMemcpyAsync(msg, res, n * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CATFHE_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CATFHE_ECUDA;
+    if (c.scheme == CATFHE_BGV) {
+        const uint64_t finv = h_invmod(factor % c.t, c.t);
+        for (size_t j = 0; j < n; j++) msg[j] = int64_t(h_mulmod(uint64_t(msg[j]), finv, c.t));
+    }
+    return CATFHE_OK;
+}
+
+}  // namespace catfhe

@@ -1,0 +1,310 @@
+"""Bit-exact parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every ciphertext limb, key limb and decrypted coefficient must be equal;
+the arithmetic is exact modular integer arithmetic on both sides.  Inputs
+are seeded: uniform ciphertexts and keys come from the ChaCha20 stream that
+each side implements on its own, messages from workloads.py.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_22227_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2503_22227_gb300 import api  # noqa: E402
+
+SEED = W.seed_for("parity-keys")
+
+
+def octx_for(p: W.Preset):
+    return oracle.Context(p.scheme, p.log_n, p.q_bits, p.p_bits, p.dnum, t=p.t,
+                          log_n_max=p.log_n_max or p.log_n, b_bits=p.b_bits)
+
+
+class Pair:
+    """GPU context + keys and oracle context + keys for one preset."""
+
+    def __init__(self, p: W.Preset, galois=()):
+        self.p = p
+        self.g = api.Context(p)
+        self.o = octx_for(p)
+        self.gk = self.g.keygen(SEED)
+        self.ok = self.o.keygen(SEED)
+        for e in galois:
+            self.gk.gen_galois(e)
+            self.ok.gen_galois(e)
+
+
+SMALL_BGV = W.Preset("bgv_small", W.BGV, 12, (55,) * 4, (60,), 4, t=65537, log_n_max=12)
+SMALL_BFV = W.Preset("bfv_small", W.BFV, 12, (55,) * 4, (60,), 4, t=65537, log_n_max=12)
+CKKS_DIGITS = W.Preset("ckks_digits", W.CKKS, 12, (45,) * 5, (50, 50), 2, log_n_max=12)
+
+
+@pytest.fixture(scope="module")
+def ckks12():
+    p = W.PRESETS["ckks_n12"]
+    pr = Pair(p)
+    for r in (1, -3):
+        e = pr.g.galois_elt(r)
+        pr.gk.gen_galois(e)
+        pr.ok.gen_galois(e)
+    conj = 2 * p.n - 1
+    pr.gk.gen_galois(conj)
+    pr.ok.gen_galois(conj)
+    return pr
+
+
+# ---------------------------------------------------------------- set-up
+
+@pytest.mark.parametrize("name", list(W.PRESETS))
+def test_prime_chains_match(name):
+    p = W.PRESETS[name]
+    g, o = api.Context(p), octx_for(p)
+    assert (g.q, g.p, g.b) == (o.q, o.p, o.b)
+    assert (g.alpha, g.beta) == (o.alpha, o.beta)
+
+
+@pytest.mark.parametrize("log_n", [12, 13, 14, 15, 16])
+def test_ntt_matches_oracle(log_n):
+    p = W.Preset("ntt", W.CKKS, log_n, (50, 61, 40), (60,), 1, log_n_max=16)
+    ctx = api.Context(p)
+    rng = np.random.default_rng(log_n)
+    count = 2
+    host = W.uniform_residues(rng, ctx.q, (count,), ctx.n)     # [count][L][N]
+    dev = torch.from_numpy(host.view(np.int64)).cuda()
+    ctx.ntt(dev)
+    got = dev.cpu().numpy().view(np.uint64)
+    for c in range(count):
+        for i, q in enumerate(ctx.q):
+            psi = oracle.min_psi(q, log_n)
+            assert np.array_equal(got[c, i], oracle.ntt(host[c, i], log_n, q, psi)), (c, i)
+    ctx.ntt(dev, inverse=True)
+    assert np.array_equal(dev.cpu().numpy().view(np.uint64), host)
+    # edge values: all q-1, all zero, a single one
+    edge = np.zeros((1, ctx.L, ctx.n), dtype=np.uint64)
+    for i, q in enumerate(ctx.q):
+        edge[0, i, :] = q - 1
+    edge[0, 0, 5] = 0
+    d = torch.from_numpy(edge.view(np.int64).copy()).cuda()
+    ctx.ntt(d)
+    got = d.cpu().numpy().view(np.uint64)
+    for i, q in enumerate(ctx.q):
+        assert np.array_equal(got[0, i], oracle.ntt(edge[0, i], log_n, q, oracle.min_psi(q, log_n)))
+
+
+# ---------------------------------------------------------------- keys, encryption
+
+@pytest.mark.parametrize("preset", [W.PRESETS["ckks_n12"], SMALL_BGV, SMALL_BFV, CKKS_DIGITS],
+                         ids=lambda p: p.name)
+def test_keys_match_oracle(preset):
+    pr = Pair(preset)
+    s, pk, ksk = pr.gk.export(0)
+    assert np.array_equal(s, pr.ok.secret())
+    assert np.array_equal(pk, pr.ok.public())
+    assert np.array_equal(ksk, pr.ok.ksk(0))
+    g = pr.g.galois_elt(2)
+    pr.gk.gen_galois(g)
+    pr.ok.gen_galois(g)
+    assert np.array_equal(pr.gk.export(g, s=False, pk=False)[2], pr.ok.ksk(g))
+
+
+@pytest.mark.parametrize("preset", [W.PRESETS["ckks_n12"], SMALL_BGV, SMALL_BFV],
+                         ids=lambda p: p.name)
+def test_encrypt_decrypt_match_oracle(preset):
+    pr = Pair(preset)
+    rng = W.rng_for("enc-" + preset.name)
+    if preset.scheme == W.CKKS:
+        msg = rng.integers(-2 ** 45, 2 ** 45, preset.n, dtype=np.int64)
+    else:
+        msg = W.int_messages(rng, preset.n, preset.t)
+    es = W.seed_for("enc-seed-" + preset.name)
+    ct = pr.g.encrypt(pr.gk, msg, es)
+    want = pr.o.encrypt(pr.ok, msg, es)
+    assert np.array_equal(pr.g.export_ct(ct)[0], want)
+    dec = pr.g.decrypt(pr.gk, ct)
+    assert np.array_equal(dec, pr.o.decrypt(pr.ok, want))
+    if preset.scheme != W.CKKS:
+        assert np.array_equal(dec, msg)
+
+
+# ---------------------------------------------------------------- hot path, CKKS
+
+def _uniform_pair(pr: Pair, level: int, count: int, tag: str):
+    a = np.stack([pr.o.ct_uniform(W.seed_for(tag), 2 * i, level) for i in range(count)])
+    b = np.stack([pr.o.ct_uniform(W.seed_for(tag), 2 * i + 1, level) for i in range(count)])
+    return a, b
+
+
+@pytest.mark.parametrize("level", [3, 2, 1])
+def test_ckks_ops_match_oracle(ckks12, level):
+    pr = ckks12
+    a, b = _uniform_pair(pr, level, 3, f"ckks-ops-{level}")
+    da, db = pr.g.import_ct(a), pr.g.import_ct(b)
+    got = pr.g.export_ct(pr.g.mul_relin(pr.gk, da, db))
+    for c in range(3):
+        assert np.array_equal(got[c], pr.o.mul_relin(pr.ok, a[c], b[c])), c
+    got = pr.g.export_ct(pr.g.add(da, db))
+    for c in range(3):
+        assert np.array_equal(got[c], pr.o.add(a[c], b[c]))
+    for r in (1, -3):
+        g = pr.g.galois_elt(r)
+        got = pr.g.export_ct(pr.g.rotate(pr.gk, da, g))
+        for c in range(3):
+            assert np.array_equal(got[c], pr.o.rotate(pr.ok, a[c], g)), (r, c)
+    conj = 2 * pr.p.n - 1
+    got = pr.g.export_ct(pr.g.rotate(pr.gk, da, conj))
+    assert np.array_equal(got[0], pr.o.rotate(pr.ok, a[0], conj))
+    if level >= 2:
+        got = pr.g.export_ct(pr.g.rescale(da))
+        for c in range(3):
+            assert np.array_equal(got[c], pr.o.rescale(a[c]))
+        got = pr.g.export_ct(pr.g.mul_relin_rescale(pr.gk, da, db))
+        for c in range(3):
+            assert np.array_equal(got[c], pr.o.rescale(pr.o.mul_relin(pr.ok, a[c], b[c]))), c
+
+
+@pytest.mark.parametrize("level", [5, 4, 3])
+def test_ckks_multi_prime_digits_match_oracle(level):
+    """alpha = 3 primes per digit and 2 special primes: partial last digits."""
+    pr = Pair(CKKS_DIGITS, galois=(5,))
+    a, b = _uniform_pair(pr, level, 2, f"digits-{level}")
+    da, db = pr.g.import_ct(a), pr.g.import_ct(b)
+    got = pr.g.export_ct(pr.g.mul_relin_rescale(pr.gk, da, db))
+    for c in range(2):
+        assert np.array_equal(got[c], pr.o.rescale(pr.o.mul_relin(pr.ok, a[c], b[c])))
+    got = pr.g.export_ct(pr.g.rotate(pr.gk, da, 5))
+    for c in range(2):
+        assert np.array_equal(got[c], pr.o.rotate(pr.ok, a[c], 5))
+
+
+def test_batched_equals_single(ckks12):
+    pr = ckks12
+    a, b = _uniform_pair(pr, 3, 5, "batch")
+    da, db = pr.g.import_ct(a), pr.g.import_ct(b)
+    batched = pr.g.export_ct(pr.g.mul_relin_rescale(pr.gk, da, db))
+    for c in range(5):
+        single = pr.g.export_ct(pr.g.mul_relin_rescale(pr.gk, da[c:c + 1], db[c:c + 1]))
+        assert np.array_equal(batched[c], single[0])
+
+
+def test_ckks_accuracy(ckks12):
+    """Decrypted slots within 2^-20 of the product at scale 2^40."""
+    pr = ckks12
+    n, scale = pr.p.n, 2.0 ** 40
+    rng = W.rng_for("gpu-ckks-accuracy")
+    za, zb = W.complex_slots(rng, n), W.complex_slots(rng, n)
+    ma, mb = oracle.encode_ckks(za, n, scale), oracle.encode_ckks(zb, n, scale)
+    ca = pr.g.encrypt(pr.gk, ma, W.seed_for("acc-a"))
+    cb = pr.g.encrypt(pr.gk, mb, W.seed_for("acc-b"))
+    prod = pr.g.mul_relin_rescale(pr.gk, ca, cb)
+    dec = pr.g.decrypt(pr.gk, prod)
+    assert np.array_equal(dec, pr.o.decrypt(pr.ok, pr.g.export_ct(prod)[0]))
+    z = oracle.decode_ckks(dec, n, scale * scale / pr.g.q[-1])
+    assert np.max(np.abs(z - za * zb)) < 2.0 ** -20
+    g = pr.g.galois_elt(1)
+    z = oracle.decode_ckks(pr.g.decrypt(pr.gk, pr.g.rotate(pr.gk, ca, g)), n, scale)
+    assert np.max(np.abs(z - np.roll(za, -1))) < 2.0 ** -20
+
+
+# ---------------------------------------------------------------- hot path, BGV / BFV
+
+@pytest.mark.parametrize("preset", [SMALL_BGV, SMALL_BFV], ids=lambda p: p.name)
+def test_integer_schemes_match_oracle(preset):
+    g5 = None
+    pr = Pair(preset)
+    g5 = pr.g.galois_elt(1)
+    pr.gk.gen_galois(g5)
+    pr.ok.gen_galois(g5)
+    level = preset.L
+    a, b = _uniform_pair(pr, level, 2, "int-" + preset.name)
+    da, db = pr.g.import_ct(a), pr.g.import_ct(b)
+    got = pr.g.export_ct(pr.g.mul_relin(pr.gk, da, db))
+    for c in range(2):
+        assert np.array_equal(got[c], pr.o.mul_relin(pr.ok, a[c], b[c])), c
+    got = pr.g.export_ct(pr.g.rotate(pr.gk, da, g5))
+    for c in range(2):
+        assert np.array_equal(got[c], pr.o.rotate(pr.ok, a[c], g5))
+    if preset.scheme == W.BGV:
+        got = pr.g.export_ct(pr.g.rescale(da))
+        assert np.array_equal(got[0], pr.o.rescale(a[0]))
+        # lower level: partial digit set
+        a2, b2 = a[:, :, :level - 1].copy(), b[:, :, :level - 1].copy()
+        got = pr.g.export_ct(pr.g.mul_relin(pr.gk, pr.g.import_ct(a2), pr.g.import_ct(b2)))
+        assert np.array_equal(got[0], pr.o.mul_relin(pr.ok, a2[0], b2[0]))
+    # decryption invariant on real encryptions
+    rng = W.rng_for("inv-" + preset.name)
+    ma, mb = W.int_messages(rng, preset.n, preset.t), W.int_messages(rng, preset.n, preset.t)
+    ca = pr.g.encrypt(pr.gk, ma, W.seed_for("inv-a"))
+    cb = pr.g.encrypt(pr.gk, mb, W.seed_for("inv-b"))
+    prod = pr.g.decrypt(pr.gk, pr.g.mul_relin(pr.gk, ca, cb))
+    n, t = preset.n, preset.t
+    # negacyclic product mod t via the oracle-independent numpy route
+    full = np.zeros(2 * n, dtype=object)
+    A, B = [int(x) for x in ma], [int(x) for x in mb]
+    conv = np.convolve(np.array(A, dtype=object), np.array(B, dtype=object))
+    full[:len(conv)] = conv
+    want = [(int(full[i]) - int(full[i + n])) % t for i in range(n)]
+    assert [int(x) for x in prod] == want
+
+
+@pytest.mark.parametrize("name", ["bfv_n14", "bgv_n14"])
+def test_integer_schemes_full_size(name):
+    """The N = 2^14, 8 x 55-bit chain, t = 65537, batch of 2 (full shape)."""
+    p = W.PRESETS[name]
+    pr = Pair(p)
+    a, b = _uniform_pair(pr, p.L, 2, "full-" + name)
+    got = pr.g.export_ct(pr.g.mul_relin(pr.gk, pr.g.import_ct(a), pr.g.import_ct(b)))
+    for c in range(2):
+        assert np.array_equal(got[c], pr.o.mul_relin(pr.ok, a[c], b[c])), c
+
+
+@pytest.mark.slow
+def test_ckks_n16_full_size():
+    """N = 2^16, L = 24, K = 4, dnum = 3: one pair through the fused op and a
+    rotation, checked limb for limb against the oracle."""
+    p = W.PRESETS["ckks_n16"]
+    pr = Pair(p)
+    g = pr.g.galois_elt(1)
+    pr.gk.gen_galois(g)
+    pr.ok.gen_galois(g)
+    a, b = _uniform_pair(pr, p.L, 1, "full-ckks16")
+    da, db = pr.g.import_ct(a), pr.g.import_ct(b)
+    got = pr.g.export_ct(pr.g.mul_relin_rescale(pr.gk, da, db))[0]
+    assert np.array_equal(got, pr.o.rescale(pr.o.mul_relin(pr.ok, a[0], b[0])))
+    got = pr.g.export_ct(pr.g.rotate(pr.gk, da, g))[0]
+    assert np.array_equal(got, pr.o.rotate(pr.ok, a[0], g))
+
+
+# ---------------------------------------------------------------- errors and edges
+
+def test_error_codes(ckks12):
+    pr = ckks12
+    a, b = _uniform_pair(pr, 1, 1, "errors")
+    da = pr.g.import_ct(a)
+    with pytest.raises(api.CatfheError) as e:
+        pr.g.rescale(da)
+    assert e.value.code == -2  # ELEVEL
+    with pytest.raises(api.CatfheError) as e:
+        pr.g.rotate(pr.gk, da, pr.g.galois_elt(7))
+    assert e.value.code == -3  # ENOKEY
+    lib = api.load()
+    import ctypes
+    out = pr.g.empty_ct(1, 1)
+    rc = lib.catfhe_mul_relin(pr.g._h, pr.gk._h, ctypes.c_void_p(da.data_ptr()),
+                              ctypes.c_void_p(da.data_ptr()), ctypes.c_void_p(out.data_ptr()), 1, 1,
+                              ctypes.c_void_p(out.data_ptr()), 16, None)
+    assert rc == -7  # EWORKSPACE
+    # count = 0 is a no-op
+    assert lib.catfhe_mul_relin(pr.g._h, pr.gk._h, ctypes.c_void_p(da.data_ptr()),
+                                ctypes.c_void_p(da.data_ptr()), ctypes.c_void_p(out.data_ptr()), 1, 0,
+                                None, 0, None) == 0
+    bfv = api.Context(SMALL_BFV)
+    x = bfv.empty_ct(1, 2)
+    with pytest.raises(api.CatfheError) as e:
+        bfv.rescale(x)
+    assert e.value.code == -6  # ESCHEME
