@@ -204,7 +204,10 @@ int catfhe_rotate(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
 
 int catfhe_rescale(catfhe_ctx *ctx, const uint64_t *a, uint64_t *out, uint32_t level,
                    uint32_t count, void *ws, size_t ws_bytes, void *stream) {
-    if (!ctx || !a || !out) return CATFHE_EINVAL;
+    if (!ctx || !a) return CATFHE_EINVAL;
+    if (ctx->c.scheme == CATFHE_BFV) return CATFHE_ESCHEME;
+    if (level < 2 || int(level) > ctx->c.L) return CATFHE_ELEVEL;
+    if (!out) return CATFHE_EINVAL;
     return op_rescale(ctx->c, a, out, level, count, ws, ws_bytes, S(stream));
 }
 
