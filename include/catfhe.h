@@ -79,10 +79,10 @@ enum { CATFHE_FORM_COEFF = 0, CATFHE_FORM_NATIVE = 1 };
  * Parameter set (paper Sec. 2.2: q = prod q_i of word-sized coprime
  * moduli; Sec. 5.1 fixes N, L and log Q per experiment).
  *   scheme     CATFHE_CKKS / _BFV / _BGV
- *   log_n      ring degree N = 2^log_n, 10 <= log_n <= 16
+ *   log_n      ring degree N = 2^log_n, 12 <= log_n <= 16
  *   log_n_max  every prime is 1 mod 2^(log_n_max+1) (>= log_n; lets one
  *              chain serve several ring degrees)
- *   L, q_bits  L ciphertext primes; prime i is the largest unused prime
+ *   L, q_bits  L <= 32 ciphertext primes; prime i is the largest unused prime
  *              below 2^q_bits[i] that is 1 mod 2^(log_n_max+1)
  *   K, p_bits  K special primes for hybrid key switching (chosen after Q)
  *   dnum       number of key-switching digits: alpha = ceil(L/dnum)
@@ -220,6 +220,17 @@ int catfhe_decrypt(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *ct,
  * runs the inverse transform (N^-1 folded in).  No workspace. */
 int catfhe_ntt(catfhe_ctx *ctx, uint64_t *limbs, uint32_t level, uint32_t count, int inverse,
                void *stream);
+
+/* Diagnostics.  catfhe_measure_int_peak times register-resident loops of
+ * independent 64-bit Shoup products by a constant and of full NTT
+ * butterflies (Shoup product + modular add + modular subtract) on the
+ * current device, filling the whole GPU; it reports the best of five
+ * launches in operations per second (either pointer may be NULL) and
+ * synchronises `stream`.  These are the integer-pipe ceilings the hot path
+ * is measured against.  catfhe_kernel_launches returns how many kernels
+ * the library has launched since it was loaded. */
+int catfhe_measure_int_peak(double *modmul_per_s, double *butterfly_per_s, void *stream);
+uint64_t catfhe_kernel_launches(void);
 
 /* Workspace bytes that `op` needs for `count` ciphertexts at `level`. */
 size_t catfhe_workspace_bytes(const catfhe_ctx *ctx, int op, uint32_t level, uint32_t count);

@@ -30,7 +30,7 @@ EXPORTS = [
     "catfhe_keys_destroy", "catfhe_keys_export", "catfhe_encrypt", "catfhe_ct_uniform",
     "catfhe_ct_import", "catfhe_ct_export", "catfhe_add", "catfhe_mul_relin",
     "catfhe_mul_relin_rescale", "catfhe_rotate", "catfhe_rescale", "catfhe_decrypt",
-    "catfhe_ntt", "catfhe_workspace_bytes",
+    "catfhe_ntt", "catfhe_workspace_bytes", "catfhe_measure_int_peak", "catfhe_kernel_launches",
 ]
 
 
@@ -91,6 +91,8 @@ def load(path: str = LIB_PATH):
             "catfhe_decrypt": (ctypes.c_int, [vp, vp, vp, u32, u64, vp, vp, sz, vp]),
             "catfhe_ntt": (ctypes.c_int, [vp, vp, u32, u32, ctypes.c_int, vp]),
             "catfhe_workspace_bytes": (sz, [vp, ctypes.c_int, u32, u32]),
+            "catfhe_measure_int_peak": (ctypes.c_int, [vp, vp, vp]),
+            "catfhe_kernel_launches": (u64, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -209,16 +211,36 @@ class Context:
                "catfhe_ct_uniform")
         return out
 
-    def import_ct(self, host: np.ndarray, form: int = FORM_COEFF):
-        """host: uint64 [count][2][level][N] -> device tensor (at-rest form)."""
-        h = np.ascontiguousarray(host, dtype=np.uint64)
-        if h.ndim == 3:
-            h = h[None]
-        count, _, level, _ = h.shape
-        out = self.empty_ct(count, level)
-        _check(load().catfhe_ct_import(self._h, h.ctypes.data_as(vp), level, count, form, _ptr(out),
-                                       _stream()), "catfhe_ct_import")
+    def import_ct(self, host, form: int = FORM_COEFF, out=None):
+        """host: uint64 numpy array, or a (pinned) CPU int64 tensor, shaped
+        [count][2][level][N] -> device tensor in the at-rest form."""
+        torch = _torch()
+        if isinstance(host, torch.Tensor):
+            assert host.device.type == "cpu" and host.is_contiguous() and host.dtype == torch.int64
+            count, _, level, _ = host.shape
+            hp = ctypes.c_void_p(host.data_ptr())
+            keep = host
+        else:
+            h = np.ascontiguousarray(host, dtype=np.uint64)
+            if h.ndim == 3:
+                h = h[None]
+            count, _, level, _ = h.shape
+            hp = h.ctypes.data_as(vp)
+            keep = h
+        out = self.empty_ct(count, level) if out is None else out
+        _check(load().catfhe_ct_import(self._h, hp, level, count, form, _ptr(out), _stream()),
+               "catfhe_ct_import")
+        del keep
         return out
+
+    def export_into(self, ct, host, form: int = FORM_NATIVE):
+        """Device ciphertexts -> a (pinned) CPU int64 tensor of the same shape."""
+        count, _, level, _ = ct.shape
+        ws = self.workspace(OP_EXPORT, level, count)
+        _check(load().catfhe_ct_export(self._h, _ptr(ct), level, count, form,
+                                       ctypes.c_void_p(host.data_ptr()), _ptr(ws), ws.numel(),
+                                       _stream()), "catfhe_ct_export")
+        return host
 
     def export_ct(self, ct, form: int = FORM_COEFF) -> np.ndarray:
         count, _, level, n = ct.shape
@@ -283,6 +305,18 @@ class Context:
         _check(load().catfhe_ntt(self._h, _ptr(limbs), level, count, int(inverse), _stream()),
                "catfhe_ntt")
         return limbs
+
+
+def measure_int_peak() -> tuple[float, float]:
+    """(Shoup modmul/s, NTT butterfly/s) ceilings of the current device."""
+    mm, bf = ctypes.c_double(), ctypes.c_double()
+    _check(load().catfhe_measure_int_peak(ctypes.byref(mm), ctypes.byref(bf), _stream()),
+           "catfhe_measure_int_peak")
+    return mm.value, bf.value
+
+
+def kernel_launches() -> int:
+    return int(load().catfhe_kernel_launches())
 
 
 class Keys:

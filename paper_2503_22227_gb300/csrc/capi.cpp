@@ -43,6 +43,7 @@ int op_export(Context &c, const uint64_t *ct, uint32_t level, uint32_t count, in
               uint64_t *host, void *ws, size_t ws_bytes_in, cudaStream_t s);
 int op_decrypt(Context &c, const Keys &k, const uint64_t *ct, uint32_t level, uint64_t factor,
                int64_t *msg, void *ws, size_t ws_bytes_in, cudaStream_t s);
+int measure_int_peak(double *modmul_per_s, double *bfly_per_s, cudaStream_t s);
 }  // namespace catfhe
 
 using namespace catfhe;
@@ -222,6 +223,12 @@ int catfhe_ntt(catfhe_ctx *ctx, uint64_t *limbs, uint32_t level, uint32_t count,
     if (!ctx || !limbs) return CATFHE_EINVAL;
     return op_ntt(ctx->c, limbs, level, count, inverse, S(stream));
 }
+
+int catfhe_measure_int_peak(double *modmul_per_s, double *butterfly_per_s, void *stream) {
+    return measure_int_peak(modmul_per_s, butterfly_per_s, S(stream));
+}
+
+uint64_t catfhe_kernel_launches(void) { return launches_total(); }
 
 size_t catfhe_workspace_bytes(const catfhe_ctx *ctx, int op, uint32_t level, uint32_t count) {
     if (!ctx) return 0;

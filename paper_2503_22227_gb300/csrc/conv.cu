@@ -229,6 +229,7 @@ int launch_conv(const Context &c, const PlanList &plans, const uint64_t *src, si
         case 16: k_conv<16><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, dst_item, dst_plan, c.log_n); break;
         default: k_conv<32><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, dst_item, dst_plan, c.log_n); break;
     }
+    note_launches(1);
     return cudaGetLastError() == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
 }
 
@@ -254,6 +255,7 @@ int launch_bfv_scale_round(const Context &c, const uint64_t *q_to_b, uint32_t q_
                                                         b_to_q_words, src, src_item, dst, dst_item,
                                                         c.log_n);
     }
+    note_launches(1);
     return cudaGetLastError() == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
 }
 

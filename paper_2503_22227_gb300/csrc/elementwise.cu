@@ -10,7 +10,10 @@
 
 namespace catfhe {
 
-static inline int ok() { return cudaGetLastError() == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA; }
+static inline int ok() {
+    note_launches(1);
+    return cudaGetLastError() == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
+}
 
 static inline dim3 coeff_grid(size_t n, uint32_t y, uint32_t z = 1) {
     return dim3(unsigned((n + 255) / 256), y, z);

@@ -116,6 +116,10 @@ struct Keys {
     std::map<uint64_t, uint64_t *> ksk;        // id -> [beta][2][L+K][N] NTT form
 };
 
+// Number of kernels this library has launched (all contexts, all threads).
+void note_launches(uint32_t k);
+uint64_t launches_total();
+
 // ----------------------------------------------------------------- launchers
 // NTT (ntt.cu)
 int launch_ntt_fwd(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,

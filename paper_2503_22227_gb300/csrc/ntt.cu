@@ -278,6 +278,7 @@ static int run_fwd(const Context &c, const uint64_t *src, uint64_t *dst, const L
     k_ntt_fwd_cols<R1, E1><<<g1, 256, 0, s>>>(src, dst, map, c.d_mods, c.d_twf, c.log_n);
     dim3 g2(unsigned((N >> R2) / (256 / ((1 << R2) >> E2))), n_limbs);
     k_ntt_fwd_rows<R2, E2><<<g2, 256, 0, s>>>(dst, map, c.d_mods, c.d_twf, c.log_n);
+    note_launches(2);
     return cudaGetLastError() == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
 }
 
@@ -289,6 +290,7 @@ static int run_inv(const Context &c, const uint64_t *src, uint64_t *dst, const L
     k_ntt_inv_rows<R2, E2><<<g2, 256, 0, s>>>(src, dst, map, c.d_mods, c.d_twi, c.log_n);
     dim3 g1(unsigned((N >> R1) / (256 / ((1 << R1) >> E1))), n_limbs);
     k_ntt_inv_cols<R1, E1><<<g1, 256, 0, s>>>(dst, map, c.d_mods, c.d_twi, c.log_n);
+    note_launches(2);
     return cudaGetLastError() == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
 }
 

@@ -1,0 +1,110 @@
+// Integer-pipe ceilings of this device for the arithmetic the hot path is
+// made of, measured by register-resident microbenchmarks (no memory traffic
+// inside the timed loop): the 64-bit Shoup product by a constant (one per
+// twiddle multiply, base-conversion weight, key product) and the full NTT
+// butterfly (Shoup product plus the modular add and subtract).  These are the
+// denominators of the "alu" roofline the benchmark reports.
+//
+// Also holds the library's kernel-launch counter.
+#include <atomic>
+
+#include "modarith.cuh"
+
+namespace catfhe {
+
+static std::atomic<uint64_t> g_launches{0};
+void note_launches(uint32_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+constexpr int kChains = 8;
+
+__global__ void __launch_bounds__(256) k_peak_modmul(uint64_t *out, uint64_t q, uint64_t w,
+                                                      uint64_t ws, int iters) {
+    const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    uint64_t x[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; j++) x[j] = (tid * 0x9E3779B97F4A7C15ull + j) % q;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int j = 0; j < kChains; j++) x[j] = shoup(x[j], w, ws, q);
+    }
+    uint64_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < kChains; j++) acc ^= x[j];
+    out[tid] = acc;
+}
+
+__global__ void __launch_bounds__(256) k_peak_bfly(uint64_t *out, uint64_t q, uint64_t w,
+                                                    uint64_t ws, int iters) {
+    const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    uint64_t a[kChains], b[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; j++) {
+        a[j] = (tid * 0x9E3779B97F4A7C15ull + j) % q;
+        b[j] = (tid * 0xC2B2AE3D27D4EB4Full + 3 * j) % q;
+    }
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int j = 0; j < kChains; j++) {
+            const uint64_t t = shoup(b[j], w, ws, q);
+            const uint64_t a0 = a[j];
+            a[j] = add_mod(a0, t, q);
+            b[j] = sub_mod(a0, t, q);
+        }
+    }
+    uint64_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < kChains; j++) acc ^= a[j] ^ b[j];
+    out[tid] = acc;
+}
+
+// Best of `reps` launches, in operations per second.
+static int time_kernel(int which, cudaStream_t s, double *rate) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CATFHE_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return CATFHE_ECUDA;
+    const void *fn = which ? (const void *)k_peak_bfly : (const void *)k_peak_modmul;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess)
+        return CATFHE_ECUDA;
+    const int blocks = sms * (per_sm > 0 ? per_sm : 1);
+    const size_t threads = size_t(blocks) * 256;
+    const int iters = 2048;
+    uint64_t *out = nullptr;
+    if (cudaMalloc(&out, threads * 8) != cudaSuccess) return CATFHE_ENOMEM;
+    const uint64_t q = 0x3ffffffffffc0001ull % 0x3fffffffffffffffull | 1;  // < 2^62, odd
+    const uint64_t w = 0x1234567890abcdefull % q;
+    const uint64_t ws = uint64_t(((unsigned __int128)w << 64) / q);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 0;
+    int rc = CATFHE_OK;
+    for (int rep = 0; rep < 6 && rc == CATFHE_OK; rep++) {
+        cudaEventRecord(e0, s);
+        if (which)
+            k_peak_bfly<<<blocks, 256, 0, s>>>(out, q, w, ws, iters);
+        else
+            k_peak_modmul<<<blocks, 256, 0, s>>>(out, q, w, ws, iters);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = CATFHE_ECUDA;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double ops = double(threads) * iters * kChains;
+        if (rep > 0 && ms > 0) best = std::max(best, ops / (ms * 1e-3));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    *rate = best;
+    return rc;
+}
+
+int measure_int_peak(double *modmul_per_s, double *bfly_per_s, cudaStream_t s) {
+    int rc = CATFHE_OK;
+    if (modmul_per_s) rc = time_kernel(0, s, modmul_per_s);
+    if (rc == CATFHE_OK && bfly_per_s) rc = time_kernel(1, s, bfly_per_s);
+    return rc;
+}
+
+}  // namespace catfhe
