@@ -24,17 +24,29 @@
 
 namespace catfhe {
 
+// Butterflies with lazy reduction (after Harvey, "Faster arithmetic for
+// number-theoretic transforms", 2014): the forward transform keeps words in
+// [0, 4q) and the inverse in [0, 2q) between stages, so each butterfly pays
+// one conditional subtraction instead of three; the last stage of each
+// transform reduces fully to [0, q).  Needs 4q < 2^64 (q < 2^62).
 __device__ __forceinline__ void ct_bfly(uint64_t &a, uint64_t &b, ulonglong2 w, uint64_t q) {
-    const uint64_t t = shoup(b, w.x, w.y, q);
-    const uint64_t a0 = a;
-    a = add_mod(a0, t, q);
-    b = sub_mod(a0, t, q);
+    const uint64_t q2 = 2 * q;
+    const uint64_t x = csub(a, q2);                  // [0, 2q)
+    const uint64_t t = shoup_lazy(b, w.x, w.y, q);   // [0, 2q)
+    a = x + t;                                       // [0, 4q)
+    b = x + q2 - t;                                  // (0, 4q)
 }
 
 __device__ __forceinline__ void gs_bfly(uint64_t &a, uint64_t &b, ulonglong2 w, uint64_t q) {
-    const uint64_t a0 = a, b0 = b;
-    a = add_mod(a0, b0, q);
-    b = shoup(a0 + q - b0, w.x, w.y, q);
+    const uint64_t q2 = 2 * q;
+    const uint64_t a0 = a, b0 = b;                   // [0, 2q)
+    a = csub(a0 + b0, q2);                           // [0, 2q)
+    b = shoup_lazy(a0 + q2 - b0, w.x, w.y, q);       // [0, 2q)
+}
+
+// [0, 4q) -> [0, q)
+__device__ __forceinline__ uint64_t reduce4(uint64_t x, uint64_t q) {
+    return csub(csub(x, 2 * q), q);
 }
 
 // ------------------------------------------------------------------ forward
@@ -141,7 +153,7 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
         }
     }
 #pragma unroll
-    for (int v = 0; v < E; v++) s[PAD(tau * E + v)] = x[v];
+    for (int v = 0; v < E; v++) s[PAD(tau * E + v)] = reduce4(x[v], q);
     __syncthreads();
 #pragma unroll
     for (int v = 0; v < E; v++) base[tau + T * v] = s[PAD(tau + T * v)];
@@ -261,7 +273,7 @@ k_ntt_inv_cols(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
         for (int v = 0; v < half; v++) {
             const uint64_t a0 = x[v], b0 = x[v + half];
             x[v] = shoup(a0 + b0, m.ninv, m.ninv_s, q);
-            x[v + half] = shoup(a0 + q - b0, m.ninvw, m.ninvw_s, q);
+            x[v + half] = shoup(a0 + 2 * q - b0, m.ninvw, m.ninvw_s, q);
         }
     }
 #pragma unroll

@@ -1,8 +1,10 @@
 // Integer-pipe ceilings of this device for the arithmetic the hot path is
 // made of, measured by register-resident microbenchmarks (no memory traffic
-// inside the timed loop): the 64-bit Shoup product by a constant (one per
-// twiddle multiply, base-conversion weight, key product) and the full NTT
-// butterfly (Shoup product plus the modular add and subtract).  These are the
+// inside the timed loop): the 64-bit Shoup product by a constant, fully
+// reduced (one per twiddle multiply, base-conversion weight, key product),
+// and the NTT butterfly exactly as the transform runs it (lazy Shoup
+// product, one conditional subtraction, the add and the subtract, words in
+// [0, 4q)).  These are the
 // denominators of the "alu" roofline the benchmark reports.
 //
 // Also holds the library's kernel-launch counter.
@@ -46,10 +48,11 @@ __global__ void __launch_bounds__(256) k_peak_bfly(uint64_t *out, uint64_t q, ui
     for (int it = 0; it < iters; it++) {
 #pragma unroll
         for (int j = 0; j < kChains; j++) {
-            const uint64_t t = shoup(b[j], w, ws, q);
-            const uint64_t a0 = a[j];
-            a[j] = add_mod(a0, t, q);
-            b[j] = sub_mod(a0, t, q);
+            // the forward transform's lazy butterfly: words in [0, 4q)
+            const uint64_t x = csub(a[j], 2 * q);
+            const uint64_t t = shoup_lazy(b[j], w, ws, q);
+            a[j] = x + t;
+            b[j] = x + 2 * q - t;
         }
     }
     uint64_t acc = 0;
