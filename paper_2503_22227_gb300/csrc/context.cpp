@@ -166,7 +166,8 @@ std::vector<uint64_t> build_plan(const PlanSpec &s) {
     std::vector<uint64_t> out(plan_words(k, T), 0);
     bool wrap = false;
     for (uint64_t q : s.dst_mod) wrap |= (q == 0);
-    out[0] = uint64_t(k) | (uint64_t(T) << 16) | (uint64_t(wrap ? 1 : 0) << 32);
+    out[0] = uint64_t(k) | (uint64_t(T) << 16) | (uint64_t(wrap ? 1 : 0) << 32) |
+             (uint64_t(s.lazy && !wrap ? 1 : 0) << 33);
     uint64_t *c = out.data() + 1;
     uint64_t *src_off = c; c += k;
     uint64_t *dst_off = c; c += T;

@@ -27,7 +27,7 @@
 namespace catfhe {
 
 struct PlanView {
-    uint32_t k, T, wrap;
+    uint32_t k, T, wrap, lazy;
     const uint64_t *src_off, *dst_off, *smod, *dmod, *pre, *pre_s, *W, *Minv, *Minv_s, *h, *Wt,
         *Mt, *post, *post_s;
 };
@@ -36,7 +36,8 @@ __device__ __forceinline__ PlanView plan_view(const uint64_t *p) {
     PlanView v;
     v.k = uint32_t(p[0] & 0xffff);
     v.T = uint32_t((p[0] >> 16) & 0xffff);
-    v.wrap = uint32_t(p[0] >> 32);
+    v.wrap = uint32_t((p[0] >> 32) & 1);
+    v.lazy = uint32_t((p[0] >> 33) & 1);
     const uint64_t *c = p + 1;
     const uint32_t k = v.k, T = v.T;
     v.src_off = c; c += k;
@@ -85,6 +86,24 @@ __device__ __forceinline__ uint64_t dot_mod(const uint64_t (&a)[KMAX], const uin
     return reduce128(acc, m);
 }
 
+// The same sum in [0, 4q) (no final conditional subtractions).
+template <int KMAX>
+__device__ __forceinline__ uint64_t dot_mod_lazy(const uint64_t (&a)[KMAX], const uint64_t *w,
+                                                 uint32_t stride, uint32_t cnt, const DevMod &m) {
+    U128 acc{0, 0};
+#pragma unroll(KMAX <= 16 ? KMAX : 1)
+    for (int i = 0; i < KMAX; i++) {
+        if (uint32_t(i) < cnt) {
+            mac(acc, a[i], w[size_t(i) * stride]);
+            if ((i & 7) == 7 && uint32_t(i + 1) < cnt) {
+                acc.lo = reduce128(acc, m);
+                acc.hi = 0;
+            }
+        }
+    }
+    return shoup_lazy(acc.hi, m.r64, m.r64_s, m.q) + shoup_lazy(acc.lo, 1, m.one_s, m.q);
+}
+
 // Turns a[] (residues, already pre-multiplied) into mixed-radix digits and
 // returns whether x > (M-1)/2.
 template <int KMAX>
@@ -120,6 +139,13 @@ __device__ __forceinline__ uint64_t eval_target(const uint64_t (&a)[KMAX], bool 
         return gt ? r - P.Mt[t] : r;
     }
     const DevMod mt = mod4(P.dmod + 4 * t);
+    if (P.lazy) {
+        // [0, 4q): one conditional subtraction fewer, for an NTT to consume
+        uint64_t r = csub(dot_mod_lazy<KMAX>(a, P.Wt + t, P.T, P.k, mt), 2 * mt.q);
+        if (gt) r += 2 * mt.q - P.Mt[t];
+        if (P.post[t] != 1) r = shoup_lazy(r, P.post[t], P.post_s[t], mt.q);
+        return r;
+    }
     uint64_t r = dot_mod<KMAX>(a, P.Wt + t, P.T, P.k, mt);
     if (gt) r = sub_mod(r, P.Mt[t], mt.q);
     if (P.post[t] != 1) r = shoup(r, P.post[t], P.post_s[t], mt.q);

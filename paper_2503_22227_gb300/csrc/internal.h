@@ -41,7 +41,9 @@ struct LimbMap {
 // Constants of one exact, centred base conversion from k source moduli to T
 // target moduli (mixed-radix form of the CRT; see conv.cu), packed into a
 // flat array of 64-bit words, sections in this order:
-//   [0]            k | T << 16 | wrap64 << 32   (wrap64: targets are 2^64)
+//   [0]            k | T << 16 | wrap64 << 32 | lazy << 33
+//                  (wrap64: targets are 2^64; lazy: outputs may lie in
+//                  [0, 4q) instead of [0, q), for an NTT to consume)
 //   src_off[k]     source limb offsets (in limbs, per item)
 //   dst_off[T]     target limb offsets
 //   smod[k][4]     source modulus: q, 2^64 mod q, its Shoup quotient, floor(2^64/q)
@@ -60,6 +62,7 @@ __host__ __device__ inline size_t plan_words(uint32_t k, uint32_t T) {
 // Source / target description of a conversion plan.  A target modulus of 0
 // means 2^64 (two's complement output).  Empty pre / post mean 1.
 struct PlanSpec {
+    bool lazy = false;
     std::vector<uint64_t> src_mod;
     std::vector<uint32_t> src_off;
     std::vector<uint64_t> pre;

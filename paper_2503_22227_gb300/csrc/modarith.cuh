@@ -26,8 +26,9 @@ __device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) 
 }
 
 // a*w mod q in [0, 2q); any 64-bit a, w < q, ws = floor(w 2^64 / q).
+// Computed as a*w + floor(a ws / 2^64) * (2^64 - q) modulo 2^64.
 __device__ __forceinline__ uint64_t shoup_lazy(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
-    return a * w - mulhi(a, ws) * q;
+    return a * w + mulhi(a, ws) * (0 - q);
 }
 
 __device__ __forceinline__ uint64_t shoup(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
@@ -38,10 +39,12 @@ struct U128 {
     uint64_t lo, hi;
 };
 
+// acc += a * b (full 128-bit product), as one multiply-add carry chain.
 __device__ __forceinline__ void mac(U128 &acc, uint64_t a, uint64_t b) {
-    uint64_t lo = a * b, hi = mulhi(a, b);
-    acc.lo += lo;
-    acc.hi += hi + (acc.lo < lo ? 1 : 0);
+    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\t"
+        "madc.hi.u64 %1, %2, %3, %1;"
+        : "+l"(acc.lo), "+l"(acc.hi)
+        : "l"(a), "l"(b));
 }
 
 // Exact x mod q for any 128-bit x.

@@ -92,6 +92,7 @@ static int modup(Context &c, const uint64_t *d2c, uint64_t *ext, uint32_t count,
     for (int j = 0; j < beta; j++) {
         const int lo = j * c.alpha, hi = std::min((j + 1) * c.alpha, level);
         PlanSpec sp;
+        sp.lazy = true;  // the lifted limbs go straight into an NTT
         for (int i = lo; i < hi; i++) {
             sp.src_mod.push_back(c.mod(i));
             sp.src_off.push_back(uint32_t(i));
@@ -193,6 +194,7 @@ static int moddown(Context &c, uint64_t *y, uint64_t *lift, uint64_t *out, const
         TRY(launch_ntt_inv(c, y, y, m, m.period * count, s));
     }
     PlanSpec sp;
+    sp.lazy = ntt_form;  // NTT schemes transform the lift before the combine
     for (int d = 0; d < Kd; d++) {
         sp.src_mod.push_back(c.mod(ext_prime(c, level, dpos[d])));
         sp.src_off.push_back(uint32_t(dpos[d]));
@@ -349,6 +351,7 @@ static int mul_relin_bfv(Context &c, const Keys &keys, const uint64_t *a, const 
     // 1. centred lift of the 4 input polys from Q_l to Q_l u B
     {
         PlanSpec sp;
+        sp.lazy = true;  // NTT'd before the tensor
         for (int i = 0; i < level; i++) {
             sp.src_mod.push_back(c.mod(i));
             sp.src_off.push_back(uint32_t(i));
@@ -434,6 +437,7 @@ static int mul_relin_bfv(Context &c, const Keys &keys, const uint64_t *a, const 
         for (int j = 0; j < beta; j++) {
             const int lo = j * c.alpha, hi = std::min((j + 1) * c.alpha, level);
             PlanSpec sp;
+            sp.lazy = true;
             for (int i = lo; i < hi; i++) {
                 sp.src_mod.push_back(c.mod(i));
                 sp.src_off.push_back(uint32_t(i));
@@ -582,6 +586,7 @@ int op_rescale(Context &c, const uint64_t *a, uint64_t *out, uint32_t level, uin
     }
     TRY(launch_ntt_inv(c, a, last, m, 2 * count, s));
     PlanSpec sp;
+    sp.lazy = true;  // NTT'd before the combine
     sp.src_mod.push_back(c.mod(lvl - 1));
     sp.src_off.push_back(0);
     for (int i = 0; i < lo; i++) {
