@@ -161,41 +161,32 @@ static void put_mod(uint64_t *w, uint64_t q) {
     w[3] = m.one_s;
 }
 
+static uint64_t neg_inv64(uint64_t m) {
+    uint64_t x = m;  // m x = 1 mod 8 for odd m; each Newton step doubles the bits
+    for (int i = 0; i < 6; i++) x *= 2 - m * x;
+    return 0 - x;
+}
+
+static uint64_t r64_mod(uint64_t m) { return (uint64_t)(((u128)1 << 64) % m); }
+
+bool plan_fits_mont(const PlanSpec &s) {
+    u128 sum = 1;
+    for (uint64_t m : s.src_mod) sum += m;
+    return sum < ((u128)1 << 64);
+}
+
 std::vector<uint64_t> build_plan(const PlanSpec &s) {
     const uint32_t k = uint32_t(s.src_mod.size()), T = uint32_t(s.dst_mod.size());
-    std::vector<uint64_t> out(plan_words(k, T), 0);
+    const bool mont = !s.exact && plan_fits_mont(s);
     bool wrap = false;
     for (uint64_t q : s.dst_mod) wrap |= (q == 0);
-    out[0] = uint64_t(k) | (uint64_t(T) << 16) | (uint64_t(wrap ? 1 : 0) << 32) |
-             (uint64_t(s.lazy && !wrap ? 1 : 0) << 33);
-    uint64_t *c = out.data() + 1;
-    uint64_t *src_off = c; c += k;
-    uint64_t *dst_off = c; c += T;
-    uint64_t *smod = c; c += 4 * k;
-    uint64_t *dmod = c; c += 4 * T;
-    uint64_t *pre = c; c += k;
-    uint64_t *pre_s = c; c += k;
-    uint64_t *W = c; c += size_t(k) * k;
-    uint64_t *Minv = c; c += k;
-    uint64_t *Minv_s = c; c += k;
-    uint64_t *h = c; c += k;
-    uint64_t *Wt = c; c += size_t(k) * T;
-    uint64_t *Mt = c; c += T;
-    uint64_t *post = c; c += T;
-    uint64_t *post_s = c;
     const auto &m = s.src_mod;
-    for (uint32_t i = 0; i < k; i++) {
-        src_off[i] = s.src_off[i];
-        put_mod(smod + 4 * i, m[i]);
-        pre[i] = s.pre.empty() ? 1 : s.pre[i] % m[i];
-        pre_s[i] = h_shoup(pre[i], m[i]);
-    }
+    // plain constants shared by both layouts
+    std::vector<uint64_t> pre(k), post(T), W(size_t(k) * k), Minv(k), h(k), Wt(size_t(k) * T), Mt(T);
+    for (uint32_t i = 0; i < k; i++) pre[i] = s.pre.empty() ? 1 : s.pre[i] % m[i];
     for (uint32_t t = 0; t < T; t++) {
-        dst_off[t] = s.dst_off[t];
-        put_mod(dmod + 4 * t, s.dst_mod[t]);
         const uint64_t p = s.dst_mod[t];
         post[t] = s.post.empty() ? 1 : (p ? s.post[t] % p : s.post[t]);
-        post_s[t] = p ? h_shoup(post[t], p) : 0;
     }
     // W[i][j] = prod_{l<i} m_l mod m_j;  Minv[j] = (prod_{l<j} m_l)^-1 mod m_j
     for (uint32_t j = 0; j < k; j++) {
@@ -207,20 +198,16 @@ std::vector<uint64_t> build_plan(const PlanSpec &s) {
         uint64_t prod = 1 % m[j];
         for (uint32_t l = 0; l < j; l++) prod = h_mulmod(prod, m[l] % m[j], m[j]);
         Minv[j] = h_invmod(prod, m[j]);
-        Minv_s[j] = h_shoup(Minv[j], m[j]);
     }
     // mixed-radix digits of (M-1)/2, whose residues are (m_i - 1)/2
     for (uint32_t j = 0; j < k; j++) {
-        uint64_t r = (m[j] - 1) / 2;
-        u128 sum = 0;
+        const uint64_t r = (m[j] - 1) / 2;
         uint64_t s_mod = 0;
-        for (uint32_t i = 0; i < j; i++) {
-            sum = (u128)h_mulmod(h[i] % m[j], W[size_t(i) * k + j], m[j]) + s_mod;
-            s_mod = (uint64_t)(sum % m[j]);
-        }
+        for (uint32_t i = 0; i < j; i++)
+            s_mod = (uint64_t)(((u128)h_mulmod(h[i] % m[j], W[size_t(i) * k + j], m[j]) + s_mod) % m[j]);
         h[j] = j == 0 ? r : h_mulmod((r + m[j] - s_mod) % m[j], Minv[j], m[j]);
     }
-    // target weights
+    // target weights prod_{l<i} m_l and M, mod p_t (mod 2^64 when p_t = 0)
     for (uint32_t t = 0; t < T; t++) {
         const uint64_t p = s.dst_mod[t];
         uint64_t acc = p ? 1 % p : 1;
@@ -230,50 +217,117 @@ std::vector<uint64_t> build_plan(const PlanSpec &s) {
         }
         Mt[t] = acc;
     }
+
+    std::vector<uint64_t> out(plan_words(k, T, mont), 0);
+    out[0] = uint64_t(k) | (uint64_t(T) << 16) | (uint64_t(wrap ? 1 : 0) << 32) |
+             (uint64_t(s.lazy && !wrap ? 1 : 0) << 33) | (uint64_t(mont ? 1 : 0) << 34);
+    uint64_t *c = out.data() + 1;
+    for (uint32_t i = 0; i < k; i++) c[i] = s.src_off[i];
+    c += k;
+    for (uint32_t t = 0; t < T; t++) c[t] = s.dst_off[t];
+    c += T;
+    if (mont) {
+        uint64_t *smod = c; c += 2 * k;
+        uint64_t *dmod = c; c += 2 * T;
+        uint64_t *C = c; c += size_t(k) * k;
+        uint64_t *hh = c; c += k;
+        uint64_t *Ct = c; c += size_t(k) * T;
+        uint64_t *Mneg = c;
+        for (uint32_t i = 0; i < k; i++) {
+            smod[2 * i] = m[i];
+            smod[2 * i + 1] = neg_inv64(m[i]);
+        }
+        for (uint32_t j = 0; j < k; j++) {
+            const uint64_t R = r64_mod(m[j]);
+            C[size_t(j) * k + j] = h_mulmod(h_mulmod(pre[j], Minv[j], m[j]), R, m[j]);
+            for (uint32_t i = 0; i < j; i++) {
+                const uint64_t wm = h_mulmod(W[size_t(i) * k + j], Minv[j], m[j]);
+                C[size_t(i) * k + j] = h_mulmod((m[j] - wm) % m[j], R, m[j]);
+            }
+            hh[j] = h[j];
+        }
+        for (uint32_t t = 0; t < T; t++) {
+            const uint64_t p = s.dst_mod[t];
+            if (!p) {
+                for (uint32_t i = 0; i < k; i++) Ct[size_t(i) * T + t] = Wt[size_t(i) * T + t];
+                Mneg[t] = Mt[t];
+                continue;
+            }
+            dmod[2 * t] = p;
+            dmod[2 * t + 1] = neg_inv64(p);
+            const uint64_t R = r64_mod(p), pr = h_mulmod(post[t], R, p);
+            for (uint32_t i = 0; i < k; i++) Ct[size_t(i) * T + t] = h_mulmod(Wt[size_t(i) * T + t], pr, p);
+            Mneg[t] = h_mulmod((p - Mt[t]) % p, pr, p);
+        }
+        return out;
+    }
+    uint64_t *smod = c; c += 4 * k;
+    uint64_t *dmod = c; c += 4 * T;
+    uint64_t *pre_v = c; c += k;
+    uint64_t *pre_s = c; c += k;
+    uint64_t *Wv = c; c += size_t(k) * k;
+    uint64_t *Minv_v = c; c += k;
+    uint64_t *Minv_s = c; c += k;
+    uint64_t *hv = c; c += k;
+    uint64_t *Wt_v = c; c += size_t(k) * T;
+    uint64_t *Mt_v = c; c += T;
+    uint64_t *post_v = c; c += T;
+    uint64_t *post_s = c;
+    for (uint32_t i = 0; i < k; i++) {
+        put_mod(smod + 4 * i, m[i]);
+        pre_v[i] = pre[i];
+        pre_s[i] = h_shoup(pre[i], m[i]);
+        Minv_v[i] = Minv[i];
+        Minv_s[i] = h_shoup(Minv[i], m[i]);
+        hv[i] = h[i];
+    }
+    for (size_t i = 0; i < W.size(); i++) Wv[i] = W[i];
+    for (uint32_t t = 0; t < T; t++) {
+        const uint64_t p = s.dst_mod[t];
+        put_mod(dmod + 4 * t, p);
+        post_v[t] = post[t];
+        post_s[t] = p ? h_shoup(post[t], p) : 0;
+        Mt_v[t] = Mt[t];
+    }
+    for (size_t i = 0; i < Wt.size(); i++) Wt_v[i] = Wt[i];
     return out;
 }
 
-const uint64_t *get_plan(Context &c, const std::string &key, const PlanSpec &spec,
-                         uint32_t *words) {
-    auto it = c.plans.find(key);
-    if (it != c.plans.end()) {
-        *words = c.plan_sizes[key];
-        return it->second;
-    }
-    std::vector<uint64_t> host = build_plan(spec);
-    uint64_t *dev = nullptr;
-    if (cudaMalloc(&dev, host.size() * 8) != cudaSuccess) return nullptr;
-    if (cudaMemcpy(dev, host.data(), host.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(dev);
-        return nullptr;
-    }
-    c.plans[key] = dev;
-    c.plan_sizes[key] = uint32_t(host.size());
-    *words = uint32_t(host.size());
-    return dev;
-}
-
-// Plan whose device copy is followed by `extra` words (BFV scale-and-round).
-const uint64_t *get_plan_extra(Context &c, const std::string &key, const PlanSpec &spec,
-                               const std::vector<uint64_t> &extra, uint32_t *words) {
-    auto it = c.plans.find(key);
-    if (it != c.plans.end()) {
-        *words = c.plan_sizes[key];
-        return it->second;
-    }
-    std::vector<uint64_t> host = build_plan(spec);
+static PlanRef upload_plan(Context &c, const std::string &key, std::vector<uint64_t> host,
+                           const std::vector<uint64_t> &extra) {
+    PlanRef ref;
     const size_t w = host.size();
+    ref.mont = ((host[0] >> 34) & 1) != 0;
     host.insert(host.end(), extra.begin(), extra.end());
     uint64_t *dev = nullptr;
-    if (cudaMalloc(&dev, host.size() * 8) != cudaSuccess) return nullptr;
+    if (cudaMalloc(&dev, host.size() * 8) != cudaSuccess) return ref;
     if (cudaMemcpy(dev, host.data(), host.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(dev);
-        return nullptr;
+        return ref;
     }
     c.plans[key] = dev;
-    c.plan_sizes[key] = uint32_t(w);
-    *words = uint32_t(w);
-    return dev;
+    c.plan_sizes[key] = uint32_t(w) | (ref.mont ? 0x80000000u : 0u);
+    ref.p = dev;
+    ref.words = uint32_t(w);
+    return ref;
+}
+
+PlanRef get_plan_extra(Context &c, const std::string &key0, const PlanSpec &spec,
+                       const std::vector<uint64_t> &extra) {
+    const std::string key = key0 + (spec.exact ? "/x" : "");
+    auto it = c.plans.find(key);
+    if (it != c.plans.end()) {
+        PlanRef ref;
+        ref.p = it->second;
+        ref.words = c.plan_sizes[key] & 0x7fffffffu;
+        ref.mont = (c.plan_sizes[key] & 0x80000000u) != 0;
+        return ref;
+    }
+    return upload_plan(c, key, build_plan(spec), extra);
+}
+
+PlanRef get_plan(Context &c, const std::string &key, const PlanSpec &spec) {
+    return get_plan_extra(c, key, spec, {});
 }
 
 }  // namespace catfhe

@@ -14,10 +14,18 @@
 //     digits of (M-1)/2 lexicographically; then x_c = x - M;
 //   target: x_c mod p = sum_i a_i [prod_{l<i} m_l]_p - [x > (M-1)/2] [M]_p.
 //
-// Every dot product is accumulated exactly in 128 bits (at most 8 products
-// of < 2^62 words per partial sum) and reduced once, so there is no
-// floating-point estimate and no approximation: the result is the
-// definition, bit for bit, whatever the order of the work.
+// Every sum is accumulated exactly in 128 bits and reduced once, so there is
+// no floating-point estimate and no approximation: the result is the
+// definition, bit for bit.  Two constant layouts exist (see internal.h):
+//
+//  - Montgomery (used whenever sum(m_i) + 1 < 2^64): every constant is
+//    stored times 2^64 mod its modulus, the mixed-radix step of a_j is ONE
+//    dot product over (r_j, a_0 .. a_{j-1}), a target is ONE dot product
+//    (plus the folded -M term when x is above (M-1)/2), and each is reduced
+//    by a single Montgomery reduction: u = lo * (-p^-1) mod 2^64,
+//    (acc + u p) / 2^64 = hi + mulhi(u, p) + [lo != 0], in [0, 2p) because
+//    acc < 2^64 p;
+//  - exact (fallback): each sum reduced by hi*(2^64 mod p) + lo (Shoup).
 //
 // One thread handles one coefficient of one item; the packed plan (a few
 // KB) sits in shared memory and every thread reads the same words
@@ -26,14 +34,20 @@
 
 namespace catfhe {
 
-struct PlanView {
+__device__ __forceinline__ void copy_plan(uint64_t *dst, const uint64_t *src, uint32_t words) {
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+}
+
+// ================================================================== exact layout
+
+struct ExactView {
     uint32_t k, T, wrap, lazy;
     const uint64_t *src_off, *dst_off, *smod, *dmod, *pre, *pre_s, *W, *Minv, *Minv_s, *h, *Wt,
         *Mt, *post, *post_s;
 };
 
-__device__ __forceinline__ PlanView plan_view(const uint64_t *p) {
-    PlanView v;
+__device__ __forceinline__ ExactView exact_view(const uint64_t *p) {
+    ExactView v;
     v.k = uint32_t(p[0] & 0xffff);
     v.T = uint32_t((p[0] >> 16) & 0xffff);
     v.wrap = uint32_t((p[0] >> 32) & 1);
@@ -66,12 +80,11 @@ __device__ __forceinline__ DevMod mod4(const uint64_t *w) {
     return m;
 }
 
-// sum_{i < cnt} a[i] * w[i * stride] mod m, exact.  KMAX <= 16 keeps the
-// digits in registers (fully unrolled); the wide variant (KMAX = 32) keeps
-// them in local memory with rolled loops.
+// sum_{i < cnt} a[i] * w[i * stride], partial sums of <= 8 products of
+// words < 2^62 reduced mod m so that 128 bits never overflow.
 template <int KMAX>
-__device__ __forceinline__ uint64_t dot_mod(const uint64_t (&a)[KMAX], const uint64_t *w,
-                                            uint32_t stride, uint32_t cnt, const DevMod &m) {
+__device__ __forceinline__ U128 dot_exact(const uint64_t (&a)[KMAX], const uint64_t *w,
+                                          uint32_t stride, uint32_t cnt, const DevMod &m) {
     U128 acc{0, 0};
 #pragma unroll(KMAX <= 16 ? KMAX : 1)
     for (int i = 0; i < KMAX; i++) {
@@ -83,36 +96,20 @@ __device__ __forceinline__ uint64_t dot_mod(const uint64_t (&a)[KMAX], const uin
             }
         }
     }
-    return reduce128(acc, m);
+    return acc;
 }
 
-// The same sum in [0, 4q) (no final conditional subtractions).
 template <int KMAX>
-__device__ __forceinline__ uint64_t dot_mod_lazy(const uint64_t (&a)[KMAX], const uint64_t *w,
-                                                 uint32_t stride, uint32_t cnt, const DevMod &m) {
-    U128 acc{0, 0};
+__device__ __forceinline__ bool mixed_radix_exact(uint64_t (&a)[KMAX], const ExactView &P) {
 #pragma unroll(KMAX <= 16 ? KMAX : 1)
-    for (int i = 0; i < KMAX; i++) {
-        if (uint32_t(i) < cnt) {
-            mac(acc, a[i], w[size_t(i) * stride]);
-            if ((i & 7) == 7 && uint32_t(i + 1) < cnt) {
-                acc.lo = reduce128(acc, m);
-                acc.hi = 0;
-            }
-        }
-    }
-    return shoup_lazy(acc.hi, m.r64, m.r64_s, m.q) + shoup_lazy(acc.lo, 1, m.one_s, m.q);
-}
-
-// Turns a[] (residues, already pre-multiplied) into mixed-radix digits and
-// returns whether x > (M-1)/2.
-template <int KMAX>
-__device__ __forceinline__ bool mixed_radix(uint64_t (&a)[KMAX], const PlanView &P) {
+    for (int i = 0; i < KMAX; i++)
+        if (uint32_t(i) < P.k && P.pre[i] != 1)
+            a[i] = shoup(a[i], P.pre[i], P.pre_s[i], P.smod[4 * i]);
 #pragma unroll(KMAX <= 16 ? KMAX : 1)
     for (int j = 1; j < KMAX; j++) {
         if (uint32_t(j) < P.k) {
             const DevMod mj = mod4(P.smod + 4 * j);
-            const uint64_t s = dot_mod<KMAX>(a, P.W + j, P.k, uint32_t(j), mj);
+            const uint64_t s = reduce128(dot_exact<KMAX>(a, P.W + j, P.k, uint32_t(j), mj), mj);
             a[j] = shoup(sub_mod(a[j], s, mj.q), P.Minv[j], P.Minv_s[j], mj.q);
         }
     }
@@ -127,10 +124,10 @@ __device__ __forceinline__ bool mixed_radix(uint64_t (&a)[KMAX], const PlanView 
     return gt;
 }
 
-// x_c mod p_t (times the post-multiplier).
+// x_c mod p_t (times the post-multiplier), in [0, p_t).
 template <int KMAX>
-__device__ __forceinline__ uint64_t eval_target(const uint64_t (&a)[KMAX], bool gt,
-                                                const PlanView &P, uint32_t t) {
+__device__ __forceinline__ uint64_t eval_exact(const uint64_t (&a)[KMAX], bool gt,
+                                               const ExactView &P, uint32_t t) {
     if (P.wrap) {
         uint64_t r = 0;
 #pragma unroll(KMAX <= 16 ? KMAX : 1)
@@ -139,67 +136,177 @@ __device__ __forceinline__ uint64_t eval_target(const uint64_t (&a)[KMAX], bool 
         return gt ? r - P.Mt[t] : r;
     }
     const DevMod mt = mod4(P.dmod + 4 * t);
-    if (P.lazy) {
-        // [0, 4q): one conditional subtraction fewer, for an NTT to consume
-        uint64_t r = csub(dot_mod_lazy<KMAX>(a, P.Wt + t, P.T, P.k, mt), 2 * mt.q);
-        if (gt) r += 2 * mt.q - P.Mt[t];
-        if (P.post[t] != 1) r = shoup_lazy(r, P.post[t], P.post_s[t], mt.q);
-        return r;
-    }
-    uint64_t r = dot_mod<KMAX>(a, P.Wt + t, P.T, P.k, mt);
+    uint64_t r = reduce128(dot_exact<KMAX>(a, P.Wt + t, P.T, P.k, mt), mt);
     if (gt) r = sub_mod(r, P.Mt[t], mt.q);
     if (P.post[t] != 1) r = shoup(r, P.post[t], P.post_s[t], mt.q);
     return r;
 }
 
+// ================================================================== Montgomery layout
+
+struct MontView {
+    uint32_t k, T, wrap, lazy;
+    const uint64_t *src_off, *dst_off, *smod, *dmod, *C, *h, *Ct, *Mneg;
+};
+
+__device__ __forceinline__ MontView mont_view(const uint64_t *p) {
+    MontView v;
+    v.k = uint32_t(p[0] & 0xffff);
+    v.T = uint32_t((p[0] >> 16) & 0xffff);
+    v.wrap = uint32_t((p[0] >> 32) & 1);
+    v.lazy = uint32_t((p[0] >> 33) & 1);
+    const uint64_t *c = p + 1;
+    const uint32_t k = v.k, T = v.T;
+    v.src_off = c; c += k;
+    v.dst_off = c; c += T;
+    v.smod = c; c += 2 * k;
+    v.dmod = c; c += 2 * T;
+    v.C = c; c += size_t(k) * k;
+    v.h = c; c += k;
+    v.Ct = c; c += size_t(k) * T;
+    v.Mneg = c;
+    return v;
+}
+
+// Montgomery reduction of acc < 2^64 p: acc 2^-64 mod p, in [0, 2p).
+__device__ __forceinline__ uint64_t redc(U128 acc, uint64_t p, uint64_t pinv) {
+    const uint64_t u = acc.lo * pinv;
+    return acc.hi + mulhi(u, p) + (acc.lo != 0 ? 1 : 0);
+}
+
 template <int KMAX>
-__device__ __forceinline__ void load_sources(uint64_t (&a)[KMAX], const PlanView &P,
-                                             const uint64_t *s, size_t x, size_t n) {
+__device__ __forceinline__ bool mixed_radix_mont(uint64_t (&a)[KMAX], const MontView &P) {
+#pragma unroll(KMAX <= 16 ? KMAX : 1)
+    for (int j = 0; j < KMAX; j++) {
+        if (uint32_t(j) < P.k) {
+            const uint64_t mj = P.smod[2 * j], minv = P.smod[2 * j + 1];
+            U128 acc{0, 0};
+            mac(acc, a[j], P.C[size_t(j) * P.k + j]);
+#pragma unroll(KMAX <= 16 ? KMAX : 1)
+            for (int i = 0; i < KMAX; i++)
+                if (i < j) mac(acc, a[i], P.C[size_t(i) * P.k + j]);
+            a[j] = csub(redc(acc, mj, minv), mj);
+        }
+    }
+    bool gt = false, decided = false;
+#pragma unroll(KMAX <= 16 ? KMAX : 1)
+    for (int i = KMAX - 1; i >= 0; i--) {
+        if (uint32_t(i) < P.k && !decided && a[i] != P.h[i]) {
+            gt = a[i] > P.h[i];
+            decided = true;
+        }
+    }
+    return gt;
+}
+
+// Two targets at once (two independent accumulation chains).
+template <int KMAX>
+__device__ __forceinline__ void eval_mont2(const uint64_t (&a)[KMAX], bool gt, const MontView &P,
+                                           uint32_t t, uint64_t &r0, uint64_t &r1) {
+    const uint32_t T = P.T;
+    U128 acc0{0, 0}, acc1{0, 0};
 #pragma unroll(KMAX <= 16 ? KMAX : 1)
     for (int i = 0; i < KMAX; i++) {
         if (uint32_t(i) < P.k) {
-            uint64_t r = s[P.src_off[i] * n + x];
-            if (P.pre[i] != 1) r = shoup(r, P.pre[i], P.pre_s[i], P.smod[4 * i]);
-            a[i] = r;
-        } else {
-            a[i] = 0;
+            mac(acc0, a[i], P.Ct[size_t(i) * T + t]);
+            mac(acc1, a[i], P.Ct[size_t(i) * T + t + 1]);
         }
+    }
+    if (gt) {
+        mac(acc0, 1, P.Mneg[t]);
+        mac(acc1, 1, P.Mneg[t + 1]);
+    }
+    const uint64_t p0 = P.dmod[2 * t], p1 = P.dmod[2 * t + 2];
+    r0 = redc(acc0, p0, P.dmod[2 * t + 1]);
+    r1 = redc(acc1, p1, P.dmod[2 * t + 3]);
+    if (!P.lazy) {
+        r0 = csub(r0, p0);
+        r1 = csub(r1, p1);
     }
 }
 
-__device__ __forceinline__ void copy_plan(uint64_t *dst, const uint64_t *src, uint32_t words) {
-    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+// x_c mod p_t (times the post-multiplier): [0, p_t), or [0, 2 p_t) if lazy.
+template <int KMAX>
+__device__ __forceinline__ uint64_t eval_mont(const uint64_t (&a)[KMAX], bool gt,
+                                              const MontView &P, uint32_t t) {
+    const uint32_t T = P.T;
+    if (P.wrap) {
+        uint64_t r = 0;
+#pragma unroll(KMAX <= 16 ? KMAX : 1)
+        for (int i = 0; i < KMAX; i++)
+            if (uint32_t(i) < P.k) r += a[i] * P.Ct[size_t(i) * T + t];
+        return gt ? r - P.Mneg[t] : r;
+    }
+    U128 acc{0, 0};
+#pragma unroll(KMAX <= 16 ? KMAX : 1)
+    for (int i = 0; i < KMAX; i++)
+        if (uint32_t(i) < P.k) mac(acc, a[i], P.Ct[size_t(i) * T + t]);
+    if (gt) mac(acc, 1, P.Mneg[t]);
+    const uint64_t p = P.dmod[2 * t];
+    const uint64_t r = redc(acc, p, P.dmod[2 * t + 1]);
+    return P.lazy ? r : csub(r, p);
 }
 
+// ================================================================== kernels
+
 template <int KMAX>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void load_sources(uint64_t (&a)[KMAX], uint32_t k,
+                                             const uint64_t *src_off, const uint64_t *s, size_t x,
+                                             size_t n) {
+#pragma unroll(KMAX <= 16 ? KMAX : 1)
+    for (int i = 0; i < KMAX; i++) a[i] = uint32_t(i) < k ? s[src_off[i] * n + x] : 0;
+}
+
+template <int KMAX, bool MONT>
+__global__ void __launch_bounds__(256, 4)
 k_conv(const PlanList plans, const uint64_t *__restrict__ src, size_t src_item, size_t src_plan,
        uint64_t *__restrict__ dst, size_t dst_item, size_t dst_plan, uint32_t log_n) {
     extern __shared__ uint64_t splan[];
     const uint64_t *gp = plans.p[blockIdx.z];
-    const uint32_t k = uint32_t(gp[0] & 0xffff), T = uint32_t((gp[0] >> 16) & 0xffff);
-    copy_plan(splan, gp, uint32_t(plan_words(k, T)));
+    copy_plan(splan, gp, uint32_t(plan_words(gp[0])));
     __syncthreads();
-    const PlanView P = plan_view(splan);
     const size_t n = size_t(1) << log_n;
     const uint64_t *s = src + blockIdx.y * src_item + blockIdx.z * src_plan;
     uint64_t *d = dst + blockIdx.y * dst_item + blockIdx.z * dst_plan;
-    for (size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
-         x += size_t(gridDim.x) * blockDim.x) {
-        uint64_t a[KMAX];
-        load_sources<KMAX>(a, P, s, x, n);
-        const bool gt = mixed_radix<KMAX>(a, P);
-        for (uint32_t t = 0; t < P.T; t++) d[P.dst_off[t] * n + x] = eval_target<KMAX>(a, gt, P, t);
+    if (MONT) {
+        const MontView P = mont_view(splan);
+        for (size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
+             x += size_t(gridDim.x) * blockDim.x) {
+            uint64_t a[KMAX];
+            load_sources<KMAX>(a, P.k, P.src_off, s, x, n);
+            const bool gt = mixed_radix_mont<KMAX>(a, P);
+            uint32_t t = 0;
+            if (!P.wrap) {
+                for (; t + 1 < P.T; t += 2) {
+                    uint64_t r0, r1;
+                    eval_mont2<KMAX>(a, gt, P, t, r0, r1);
+                    d[P.dst_off[t] * n + x] = r0;
+                    d[P.dst_off[t + 1] * n + x] = r1;
+                }
+            }
+            for (; t < P.T; t++) d[P.dst_off[t] * n + x] = eval_mont<KMAX>(a, gt, P, t);
+        }
+    } else {
+        const ExactView P = exact_view(splan);
+        for (size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
+             x += size_t(gridDim.x) * blockDim.x) {
+            uint64_t a[KMAX];
+            load_sources<KMAX>(a, P.k, P.src_off, s, x, n);
+            const bool gt = mixed_radix_exact<KMAX>(a, P);
+            for (uint32_t t = 0; t < P.T; t++) d[P.dst_off[t] * n + x] = eval_exact<KMAX>(a, gt, P, t);
+        }
     }
 }
 
 // BFV scale-and-round: see launch_bfv_scale_round in internal.h.  Plan
-// p_qb lifts [t x]_Q to B: its pre[] is t mod q_i, its post[] Q^-1 mod b_j,
-// and its dst_off[] locate x_b inside the source item (nothing is written
-// through it).  tq[2j], tq[2j+1] = t Q^-1 mod b_j and its Shoup quotient.
-// Plan p_bq lifts z = round(t x / Q) (centred in B) back to Q.
+// p_qb lifts [t x]_Q to B with t folded in as the source pre-multiplier and
+// Q^-1 mod b_j as the target post-multiplier; its dst_off[] locate x_b
+// inside the source item (nothing is written through it).  tq[2j], tq[2j+1]
+// = t Q^-1 mod b_j and its Shoup quotient.  Plan p_bq lifts
+// z = round(t x / Q) (centred in B) back to Q.  Both plans use the
+// Montgomery layout (the host checks the bound).
 template <int KQ, int KB>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_bfv_scale_round(const uint64_t *__restrict__ p_qb, const uint64_t *__restrict__ p_bq,
                   const uint64_t *__restrict__ tq, uint32_t w_qb, uint32_t w_bq,
                   const uint64_t *__restrict__ src, size_t src_item, uint64_t *__restrict__ dst,
@@ -211,22 +318,22 @@ k_bfv_scale_round(const uint64_t *__restrict__ p_qb, const uint64_t *__restrict_
     const uint32_t nbq = uint32_t((p_qb[0] >> 16) & 0xffff);
     copy_plan(s_tq, tq, 2 * nbq);
     __syncthreads();
-    const PlanView A = plan_view(s_qb), B = plan_view(s_bq);
+    const MontView A = mont_view(s_qb), B = mont_view(s_bq);
     const size_t n = size_t(1) << log_n;
     const uint64_t *s = src + blockIdx.y * src_item;
     uint64_t *d = dst + blockIdx.y * dst_item;
     for (size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
          x += size_t(gridDim.x) * blockDim.x) {
         uint64_t a[KQ];
-        load_sources<KQ>(a, A, s, x, n);  // t x_i mod q_i (pre = t)
-        const bool gt = mixed_radix<KQ>(a, A);
+        load_sources<KQ>(a, A.k, A.src_off, s, x, n);
+        const bool gt = mixed_radix_mont<KQ>(a, A);
         uint64_t z[KB];
 #pragma unroll(KB <= 16 ? KB : 1)
         for (int j = 0; j < KB; j++) {
             if (uint32_t(j) < A.T) {
-                // [t x]_Q Q^-1 mod b_j (post = Q^-1), and t Q^-1 x_b
-                const uint64_t l = eval_target<KQ>(a, gt, A, j);
-                const uint64_t bq = A.dmod[4 * j];
+                // [t x]_Q Q^-1 mod b_j, and t Q^-1 x_b
+                const uint64_t l = eval_mont<KQ>(a, gt, A, j);
+                const uint64_t bq = A.dmod[2 * j];
                 const uint64_t xb = s[A.dst_off[j] * n + x];
                 const uint64_t txb = shoup(xb, s_tq[2 * j], s_tq[2 * j + 1], bq);
                 z[j] = sub_mod(txb, l, bq);
@@ -234,27 +341,38 @@ k_bfv_scale_round(const uint64_t *__restrict__ p_qb, const uint64_t *__restrict_
                 z[j] = 0;
             }
         }
-        const bool gz = mixed_radix<KB>(z, B);
-        for (uint32_t t = 0; t < B.T; t++) d[B.dst_off[t] * n + x] = eval_target<KB>(z, gz, B, t);
+        const bool gz = mixed_radix_mont<KB>(z, B);
+        for (uint32_t t = 0; t < B.T; t++) d[B.dst_off[t] * n + x] = eval_mont<KB>(z, gz, B, t);
     }
 }
 
 static int pick_kmax(uint32_t k) { return k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32; }
 
+template <bool MONT>
+static void run_conv(int kmax, dim3 grid, size_t sm, cudaStream_t s, const PlanList &plans,
+                     const uint64_t *src, size_t src_item, size_t src_plan, uint64_t *dst,
+                     size_t dst_item, size_t dst_plan, uint32_t log_n) {
+    switch (kmax) {
+        case 4: k_conv<4, MONT><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, dst_item, dst_plan, log_n); break;
+        case 8: k_conv<8, MONT><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, dst_item, dst_plan, log_n); break;
+        case 16: k_conv<16, MONT><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, dst_item, dst_plan, log_n); break;
+        default: k_conv<32, MONT><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, dst_item, dst_plan, log_n); break;
+    }
+}
+
 int launch_conv(const Context &c, const PlanList &plans, const uint64_t *src, size_t src_item,
                 size_t src_plan, uint64_t *dst, size_t dst_item, size_t dst_plan, uint32_t items,
                 cudaStream_t s) {
     if (plans.n == 0 || items == 0) return CATFHE_OK;
-    const uint32_t kmax = plans.kmax, words = plans.words;
     const size_t n = c.n;
     dim3 grid(unsigned((n + 1023) / 1024), items, plans.n);
-    const size_t sm = size_t(words) * 8;
-    switch (pick_kmax(kmax)) {
-        case 4: k_conv<4><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, dst_item, dst_plan, c.log_n); break;
-        case 8: k_conv<8><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, dst_item, dst_plan, c.log_n); break;
-        case 16: k_conv<16><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, dst_item, dst_plan, c.log_n); break;
-        default: k_conv<32><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, dst_item, dst_plan, c.log_n); break;
-    }
+    const size_t sm = size_t(plans.words) * 8;
+    if (plans.mont)
+        run_conv<true>(pick_kmax(plans.kmax), grid, sm, s, plans, src, src_item, src_plan, dst,
+                       dst_item, dst_plan, c.log_n);
+    else
+        run_conv<false>(pick_kmax(plans.kmax), grid, sm, s, plans, src, src_item, src_plan, dst,
+                        dst_item, dst_plan, c.log_n);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
 }

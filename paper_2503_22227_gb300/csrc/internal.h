@@ -40,29 +40,37 @@ struct LimbMap {
 
 // Constants of one exact, centred base conversion from k source moduli to T
 // target moduli (mixed-radix form of the CRT; see conv.cu), packed into a
-// flat array of 64-bit words, sections in this order:
-//   [0]            k | T << 16 | wrap64 << 32 | lazy << 33
-//                  (wrap64: targets are 2^64; lazy: outputs may lie in
-//                  [0, 4q) instead of [0, q), for an NTT to consume)
-//   src_off[k]     source limb offsets (in limbs, per item)
-//   dst_off[T]     target limb offsets
-//   smod[k][4]     source modulus: q, 2^64 mod q, its Shoup quotient, floor(2^64/q)
-//   dmod[T][4]     target modulus, same four words
-//   pre[k], pre_s[k]      source pre-multiplier (Shoup pair)
-//   W[k][k]        W[i][j] = prod_{l<i} m_l mod m_j
-//   Minv[k], Minv_s[k]    (prod_{l<j} m_l)^-1 mod m_j
-//   h[k]           mixed-radix digits of (M-1)/2, M = prod m_l
-//   Wt[k][T]       prod_{l<i} m_l mod p_t
-//   Mt[T]          M mod p_t
-//   post[T], post_s[T]    target post-multiplier (Shoup pair)
-__host__ __device__ inline size_t plan_words(uint32_t k, uint32_t T) {
-    return 1 + 10 * size_t(k) + 8 * size_t(T) + size_t(k) * k + size_t(k) * T;
+// flat array of 64-bit words.  Word 0 is the header
+//   k | T << 16 | wrap64 << 32 | lazy << 33 | mont << 34
+// (wrap64: targets are 2^64; lazy: outputs may lie in [0, 2q) instead of
+// [0, q), for an NTT to consume; mont: the Montgomery layout below).
+// Then src_off[k], dst_off[T] (limb offsets per item) and
+//  exact layout:  smod[k][4] (q, 2^64 mod q, its Shoup quotient, floor(2^64/q)),
+//                 dmod[T][4], pre[k], pre_s[k], W[k][k] (prod_{l<i} m_l mod m_j),
+//                 Minv[k], Minv_s[k] ((prod_{l<j} m_l)^-1 mod m_j), h[k]
+//                 (mixed-radix digits of (M-1)/2), Wt[k][T] (prod_{l<i} m_l
+//                 mod p_t), Mt[T] (M mod p_t), post[T], post_s[T];
+//  Montgomery layout (every constant times 2^64 mod its modulus, so one
+//                 Montgomery reduction per sum returns the plain value):
+//                 smod[k][2] (m, -m^-1 mod 2^64), dmod[T][2],
+//                 C[k][k] (row i, column j: the weight of digit a_i, or for
+//                 i = j of the residue r_j, in the mixed-radix step of a_j),
+//                 h[k], Ct[k][T] (weight of a_i for target t, post-multiplier
+//                 folded in), Mneg[T] (-M mod p_t, post-multiplier folded in).
+__host__ __device__ inline size_t plan_words(uint32_t k, uint32_t T, bool mont) {
+    return mont ? 1 + 4 * size_t(k) + 4 * size_t(T) + size_t(k) * k + size_t(k) * T
+                : 1 + 10 * size_t(k) + 8 * size_t(T) + size_t(k) * k + size_t(k) * T;
+}
+__host__ __device__ inline size_t plan_words(uint64_t header) {
+    return plan_words(uint32_t(header & 0xffff), uint32_t((header >> 16) & 0xffff),
+                      ((header >> 34) & 1) != 0);
 }
 
 // Source / target description of a conversion plan.  A target modulus of 0
 // means 2^64 (two's complement output).  Empty pre / post mean 1.
 struct PlanSpec {
     bool lazy = false;
+    bool exact = false;  // force the exact layout (else Montgomery when it fits)
     std::vector<uint64_t> src_mod;
     std::vector<uint32_t> src_off;
     std::vector<uint64_t> pre;
@@ -71,6 +79,18 @@ struct PlanSpec {
     std::vector<uint64_t> post;
 };
 std::vector<uint64_t> build_plan(const PlanSpec &s);
+// The Montgomery layout needs sum(src_mod) + 1 < 2^64 (every accumulated sum
+// stays below 2^64 times its modulus).
+bool plan_fits_mont(const PlanSpec &s);
+struct PlanRef {
+    const uint64_t *p = nullptr;  // device copy
+    uint32_t words = 0;
+    bool mont = false;
+};
+struct Context;
+PlanRef get_plan(Context &c, const std::string &key, const PlanSpec &spec);
+PlanRef get_plan_extra(Context &c, const std::string &key, const PlanSpec &spec,
+                       const std::vector<uint64_t> &extra);
 
 // Up to this many plans run in one launch (grid.z).
 struct PlanList {
@@ -78,6 +98,7 @@ struct PlanList {
     uint32_t n;      // plans in the launch
     uint32_t kmax;   // largest source count among them
     uint32_t words;  // largest packed size among them
+    uint32_t mont;   // all plans use the Montgomery layout
 };
 
 // Host-side prime record.

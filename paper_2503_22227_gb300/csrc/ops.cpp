@@ -15,10 +15,6 @@
 
 namespace catfhe {
 
-const uint64_t *get_plan(Context &c, const std::string &key, const PlanSpec &spec,
-                         uint32_t *words);
-const uint64_t *get_plan_extra(Context &c, const std::string &key, const PlanSpec &spec,
-                               const std::vector<uint64_t> &extra, uint32_t *words);
 
 #define TRY(x)                      \
     do {                            \
@@ -57,6 +53,26 @@ static int get_ws(Context &c, void *ws, size_t ws_bytes, size_t need, char **out
     return CATFHE_OK;
 }
 
+// One launch's plans, all in one layout: Montgomery when every plan fits it.
+static int make_list(Context &c, const std::vector<std::pair<std::string, PlanSpec>> &specs,
+                     PlanList &pl) {
+    bool all = true;
+    for (const auto &s : specs) all = all && plan_fits_mont(s.second);
+    pl = PlanList{};
+    pl.n = uint32_t(specs.size());
+    pl.mont = all ? 1 : 0;
+    for (size_t i = 0; i < specs.size(); i++) {
+        PlanSpec sp = specs[i].second;
+        sp.exact = !all;
+        const PlanRef r = get_plan(c, specs[i].first, sp);
+        if (!r.p) return CATFHE_ENOMEM;
+        pl.p[i] = r.p;
+        pl.kmax = std::max<uint32_t>(pl.kmax, uint32_t(sp.src_mod.size()));
+        pl.words = std::max(pl.words, r.words);
+    }
+    return CATFHE_OK;
+}
+
 static LimbMap map_identity(uint32_t limbs, uint32_t first_prime = 0) {
     LimbMap m{};
     m.period = limbs;
@@ -87,8 +103,7 @@ static int ext_prime(const Context &c, int level, int i) { return i < level ? i 
 static int modup(Context &c, const uint64_t *d2c, uint64_t *ext, uint32_t count, int level,
                  bool own_too, cudaStream_t s) {
     const int M = level + c.K, beta = (level + c.alpha - 1) / c.alpha;
-    PlanList pl{};
-    pl.n = beta;
+    std::vector<std::pair<std::string, PlanSpec>> specs;
     for (int j = 0; j < beta; j++) {
         const int lo = j * c.alpha, hi = std::min((j + 1) * c.alpha, level);
         PlanSpec sp;
@@ -102,14 +117,12 @@ static int modup(Context &c, const uint64_t *d2c, uint64_t *ext, uint32_t count,
             sp.dst_mod.push_back(c.mod(ext_prime(c, level, i)));
             sp.dst_off.push_back(uint32_t(i));
         }
-        uint32_t w = 0;
-        const std::string key = "modup/" + std::to_string(level) + "/" + std::to_string(j) +
-                                (own_too ? "/own" : "");
-        pl.p[j] = get_plan(c, key, sp, &w);
-        if (!pl.p[j]) return CATFHE_ENOMEM;
-        pl.kmax = std::max<uint32_t>(pl.kmax, uint32_t(hi - lo));
-        pl.words = std::max(pl.words, w);
+        specs.emplace_back("modup/" + std::to_string(level) + "/" + std::to_string(j) +
+                               (own_too ? "/own" : ""),
+                           sp);
     }
+    PlanList pl;
+    TRY(make_list(c, specs, pl));
     const size_t n = c.n;
     return launch_conv(c, pl, d2c, size_t(level) * n, 0, ext, size_t(beta) * M * n, size_t(M) * n,
                        count, s);
@@ -207,13 +220,8 @@ static int moddown(Context &c, uint64_t *y, uint64_t *lift, uint64_t *out, const
         for (int d = 0; d < Kd; d++) sp.pre.push_back(h_invmod(c.t % sp.src_mod[d], sp.src_mod[d]));
         for (int i = 0; i < lo; i++) sp.post.push_back(c.t % c.mod(i));
     }
-    uint32_t w = 0;
-    PlanList pl{};
-    pl.n = 1;
-    pl.kmax = uint32_t(Kd);
-    pl.p[0] = get_plan(c, "moddown/" + std::to_string(level) + (fused ? "/f" : ""), sp, &w);
-    if (!pl.p[0]) return CATFHE_ENOMEM;
-    pl.words = w;
+    PlanList pl;
+    TRY(make_list(c, {{"moddown/" + std::to_string(level) + (fused ? "/f" : ""), sp}}, pl));
     TRY(launch_conv(c, pl, y, size_t(M) * n, 0, lift, size_t(lo) * n, 0, 2 * count, s));
     if (ntt_form) {
         LimbMap m = map_identity(uint32_t(lo));
@@ -360,13 +368,8 @@ static int mul_relin_bfv(Context &c, const Keys &keys, const uint64_t *a, const 
             sp.dst_mod.push_back(c.mod(i < level ? i : c.pb(i - level)));
             sp.dst_off.push_back(uint32_t(i));
         }
-        uint32_t w = 0;
-        PlanList pl{};
-        pl.n = 1;
-        pl.kmax = uint32_t(level);
-        pl.p[0] = get_plan(c, "bfv_lift/" + std::to_string(level), sp, &w);
-        if (!pl.p[0]) return CATFHE_ENOMEM;
-        pl.words = w;
+        PlanList pl;
+        TRY(make_list(c, {{"bfv_lift/" + std::to_string(level), sp}}, pl));
         // items: (ct, poly) for a then for b
         TRY(launch_conv(c, pl, a, size_t(level) * n, 0, k.xin, size_t(kb) * n, 0, 2 * count, s));
         TRY(launch_conv(c, pl, b, size_t(level) * n, 0, k.xin + size_t(count) * 2 * kb * n,
@@ -420,11 +423,12 @@ static int mul_relin_bfv(Context &c, const Keys &keys, const uint64_t *a, const 
             B.dst_mod.push_back(c.mod(i));
             B.dst_off.push_back(uint32_t(i));
         }
-        uint32_t wa = 0, wb = 0;
-        const uint64_t *pa = get_plan_extra(c, "bfv_sr_a/" + std::to_string(level), A, tq, &wa);
-        const uint64_t *pb = get_plan(c, "bfv_sr_b/" + std::to_string(level), B, &wb);
-        if (!pa || !pb) return CATFHE_ENOMEM;
-        TRY(launch_bfv_scale_round(c, pa, wa, pb, wb, k.tens, size_t(kb) * n, k.dq,
+        // the fused kernel needs both conversions in the Montgomery layout
+        if (!plan_fits_mont(A) || !plan_fits_mont(B)) return CATFHE_EINVAL;
+        const PlanRef pa = get_plan_extra(c, "bfv_sr_a/" + std::to_string(level), A, tq);
+        const PlanRef pb = get_plan(c, "bfv_sr_b/" + std::to_string(level), B);
+        if (!pa.p || !pb.p) return CATFHE_ENOMEM;
+        TRY(launch_bfv_scale_round(c, pa.p, pa.words, pb.p, pb.words, k.tens, size_t(kb) * n, k.dq,
                                    size_t(level) * n, 3 * count, s));
     }
     // 4. relinearise d2' (coefficient form) and add (d0', d1')
@@ -432,8 +436,7 @@ static int mul_relin_bfv(Context &c, const Keys &keys, const uint64_t *a, const 
     // ModUp reads the digit limbs of d2' per ct: item stride 3*level*N
     {
         const int M = level + c.K, beta = (level + c.alpha - 1) / c.alpha;
-        PlanList pl{};
-        pl.n = beta;
+        std::vector<std::pair<std::string, PlanSpec>> specs;
         for (int j = 0; j < beta; j++) {
             const int lo = j * c.alpha, hi = std::min((j + 1) * c.alpha, level);
             PlanSpec sp;
@@ -446,13 +449,11 @@ static int mul_relin_bfv(Context &c, const Keys &keys, const uint64_t *a, const 
                 sp.dst_mod.push_back(c.mod(ext_prime(c, level, i)));
                 sp.dst_off.push_back(uint32_t(i));
             }
-            uint32_t w = 0;
-            pl.p[j] = get_plan(c, "modup/" + std::to_string(level) + "/" + std::to_string(j) + "/own",
-                               sp, &w);
-            if (!pl.p[j]) return CATFHE_ENOMEM;
-            pl.kmax = std::max<uint32_t>(pl.kmax, uint32_t(hi - lo));
-            pl.words = std::max(pl.words, w);
+            specs.emplace_back("modup/" + std::to_string(level) + "/" + std::to_string(j) + "/own",
+                               sp);
         }
+        PlanList pl;
+        TRY(make_list(c, specs, pl));
         TRY(launch_conv(c, pl, d2, size_t(3) * level * n, 0, k.ext, size_t(beta) * M * n,
                         size_t(M) * n, count, s));
     }
@@ -597,13 +598,8 @@ int op_rescale(Context &c, const uint64_t *a, uint64_t *out, uint32_t level, uin
         sp.pre.push_back(h_invmod(c.t % c.mod(lvl - 1), c.mod(lvl - 1)));
         for (int i = 0; i < lo; i++) sp.post.push_back(c.t % c.mod(i));
     }
-    uint32_t w = 0;
-    PlanList pl{};
-    pl.n = 1;
-    pl.kmax = 1;
-    pl.p[0] = get_plan(c, "rescale/" + std::to_string(lvl), sp, &w);
-    if (!pl.p[0]) return CATFHE_ENOMEM;
-    pl.words = w;
+    PlanList pl;
+    TRY(make_list(c, {{"rescale/" + std::to_string(lvl), sp}}, pl));
     TRY(launch_conv(c, pl, last, n, 0, lift, size_t(lo) * n, 0, 2 * count, s));
     LimbMap ml = map_identity(uint32_t(lo));
     TRY(launch_ntt_fwd(c, lift, lift, ml, uint32_t(2 * lo) * count, s));
@@ -989,13 +985,8 @@ int op_decrypt(Context &c, const Keys &k, const uint64_t *ct, uint32_t level, ui
             sp.post.push_back((c.t - h_invmod(qt, c.t)) % c.t);
         }
     }
-    uint32_t w = 0;
-    PlanList pl{};
-    pl.n = 1;
-    pl.kmax = level;
-    pl.p[0] = get_plan(c, key, sp, &w);
-    if (!pl.p[0]) return CATFHE_ENOMEM;
-    pl.words = w;
+    PlanList pl;
+    TRY(make_list(c, {{key, sp}}, pl));
     TRY(launch_conv(c, pl, x, 0, 0, reinterpret_cast<uint64_t *>(res), 0, 0, 1, s));
     if (cudaMemcpyAsync(msg, res, n * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CATFHE_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return CATFHE_ECUDA;
