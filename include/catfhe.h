@@ -206,6 +206,25 @@ int catfhe_rotate(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
 int catfhe_rescale(catfhe_ctx *ctx, const uint64_t *a, uint64_t *out, uint32_t level,
                    uint32_t count, void *ws, size_t ws_bytes, void *stream);
 
+/* catfhe_rescale without any device allocation, for callers that may not
+ * allocate device memory while they run (a host callback, a loop whose
+ * memory budget is fixed at start-up, a plugin whose host process owns all
+ * device allocations).  The paper has no counterpart; the result is the
+ * same as catfhe_rescale's, bit for bit.
+ * Scratch: a 32 MiB array that the library reserves statically on every
+ * GPU that loads it (held until the process exits); enough for count
+ * ciphertexts when 16 KiB + 16 * count * level * N bytes fit in 32 MiB
+ * (one N = 2^16 ciphertext at level 24), else CATFHE_EWORKSPACE and nothing
+ * is enqueued.  No call allocates or frees memory.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  All calls share the
+ * array and it keeps the last call's contents (nothing in it needs to start
+ * at zero); calls whose device work overlaps race on it, so order them on
+ * one stream.  Inputs and outputs are caller-owned device buffers as for
+ * catfhe_rescale; `out` must not alias `a`. */
+int catfhe_rescale_noalloc(catfhe_ctx *ctx, const uint64_t *a, uint64_t *out, uint32_t level,
+                           uint32_t count, void *stream);
+
 /* Decryption of one ciphertext at `level` into host msg (int64[N]):
  * x = [c0 + c1 s]_{Q_l} centred; CKKS: x as two's complement (exact when
  * |x| < 2^63); BFV: round(t x / Q_l) mod t; BGV: x factor^-1 mod t where

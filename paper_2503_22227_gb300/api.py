@@ -31,6 +31,7 @@ EXPORTS = [
     "catfhe_ct_import", "catfhe_ct_export", "catfhe_add", "catfhe_mul_relin",
     "catfhe_mul_relin_rescale", "catfhe_rotate", "catfhe_rescale", "catfhe_decrypt",
     "catfhe_ntt", "catfhe_workspace_bytes", "catfhe_measure_int_peak", "catfhe_kernel_launches",
+    "catfhe_rescale_noalloc",
 ]
 
 
@@ -93,6 +94,7 @@ def load(path: str = LIB_PATH):
             "catfhe_workspace_bytes": (sz, [vp, ctypes.c_int, u32, u32]),
             "catfhe_measure_int_peak": (ctypes.c_int, [vp, vp, vp]),
             "catfhe_kernel_launches": (u64, []),
+            "catfhe_rescale_noalloc": (ctypes.c_int, [vp, vp, vp, u32, u32, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -297,6 +299,14 @@ class Context:
         ws = self.workspace(OP_RESCALE, level, count)
         _check(load().catfhe_rescale(self._h, _ptr(a), _ptr(out), level, count, _ptr(ws), ws.numel(),
                                      _stream()), "catfhe_rescale")
+        return out
+
+    def rescale_noalloc(self, a, out):
+        """catfhe_rescale_noalloc: the rescale with the library's static
+        scratch, for callers that cannot allocate device memory."""
+        count, _, level, _ = a.shape
+        _check(load().catfhe_rescale_noalloc(self._h, _ptr(a), _ptr(out), level, count, _stream()),
+               "catfhe_rescale_noalloc")
         return out
 
     def ntt(self, limbs, inverse: bool = False):

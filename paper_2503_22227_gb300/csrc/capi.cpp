@@ -44,6 +44,8 @@ int op_export(Context &c, const uint64_t *ct, uint32_t level, uint32_t count, in
 int op_decrypt(Context &c, const Keys &k, const uint64_t *ct, uint32_t level, uint64_t factor,
                int64_t *msg, void *ws, size_t ws_bytes_in, cudaStream_t s);
 int measure_int_peak(double *modmul_per_s, double *bfly_per_s, cudaStream_t s);
+int op_rescale_noalloc_impl(Context &c, const uint64_t *a, uint64_t *out, uint32_t level,
+                            uint32_t count, cudaStream_t s);
 }  // namespace catfhe
 
 using namespace catfhe;
@@ -210,6 +212,15 @@ int catfhe_rescale(catfhe_ctx *ctx, const uint64_t *a, uint64_t *out, uint32_t l
     if (level < 2 || int(level) > ctx->c.L) return CATFHE_ELEVEL;
     if (!out) return CATFHE_EINVAL;
     return op_rescale(ctx->c, a, out, level, count, ws, ws_bytes, S(stream));
+}
+
+int catfhe_rescale_noalloc(catfhe_ctx *ctx, const uint64_t *a, uint64_t *out, uint32_t level,
+                           uint32_t count, void *stream) {
+    if (!ctx || !a) return CATFHE_EINVAL;
+    if (ctx->c.scheme == CATFHE_BFV) return CATFHE_ESCHEME;
+    if (level < 2 || int(level) > ctx->c.L) return CATFHE_ELEVEL;
+    if (!out) return CATFHE_EINVAL;
+    return op_rescale_noalloc_impl(ctx->c, a, out, level, count, S(stream));
 }
 
 int catfhe_decrypt(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *ct, uint32_t level,
