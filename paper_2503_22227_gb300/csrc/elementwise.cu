@@ -48,67 +48,65 @@ int launch_tensor(const Context &c, const TensorArgs &a, uint32_t count, cudaStr
 // ------------------------------------------------------------------ key-switch inner product
 
 // y_p[i] = sum_j c_j[i] * key_j[p][i] (+ P * add_p[i] on ciphertext primes).
-// One thread owns one coefficient of one extended limb for the whole batch:
-// it loads the 2 beta key words once and reuses them for every ciphertext,
-// so the evaluation key crosses HBM once per batch, not once per ciphertext.
+// The batch item is the fastest-varying block index, so the CTAs of all
+// ciphertexts that read one block of the evaluation key are dispatched back
+// to back: the key crosses HBM once per batch and is served from L2 after.
 template <int BMAX>
 __global__ void __launch_bounds__(256)
-k_ip(const IpArgs A, uint32_t count, const DevMod *__restrict__ mods, uint32_t log_n) {
+k_ip(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
     const size_t n = size_t(1) << log_n;
-    const size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const uint32_t i = blockIdx.y;
+    const uint32_t item = blockIdx.x, i = blockIdx.z;
+    const size_t x = size_t(blockIdx.y) * blockDim.x + threadIdx.x;
     if (x >= n) return;
     const DevMod m = mods[A.prime[i]];
     const uint32_t KL = A.L + A.K;
-    uint64_t kb[BMAX], ka[BMAX];
+    const bool own_here = A.own != nullptr && i < A.level;
+    const uint32_t own_digit = own_here ? i / A.alpha : 0xffffffffu;
+    const uint64_t *ext = A.ext + item * A.ext_item;
+    uint64_t cj[BMAX], kb[BMAX], ka[BMAX];
 #pragma unroll
     for (int j = 0; j < BMAX; j++) {
         if (uint32_t(j) < A.beta) {
+            cj[j] = (uint32_t(j) == own_digit) ? A.own[item * A.own_item + size_t(i) * n + x]
+                                               : ext[(size_t(j) * A.M + i) * n + x];
             kb[j] = A.key[((size_t(j) * 2 + 0) * KL + A.key_limb[i]) * n + x];
             ka[j] = A.key[((size_t(j) * 2 + 1) * KL + A.key_limb[i]) * n + x];
         }
     }
-    const bool own_here = A.own != nullptr && i < A.level;
-    const uint32_t own_digit = own_here ? i / A.alpha : 0xffffffffu;
     const bool fold = i < A.level && A.pfac[i] != 0;
-    for (uint32_t item = 0; item < count; item++) {
-        const uint64_t *ext = A.ext + item * A.ext_item;
-        U128 acc0{0, 0}, acc1{0, 0};
-#pragma unroll
-        for (int j = 0; j < BMAX; j++) {
-            if (uint32_t(j) < A.beta) {
-                const uint64_t cj = (uint32_t(j) == own_digit)
-                                        ? A.own[item * A.own_item + size_t(i) * n + x]
-                                        : ext[(size_t(j) * A.M + i) * n + x];
-                mac(acc0, cj, kb[j]);
-                mac(acc1, cj, ka[j]);
-            }
-        }
-        uint64_t y0 = reduce128(acc0, m), y1 = reduce128(acc1, m);
-        if (fold) {
-            if (A.add0)
-                y0 = add_mod(y0, shoup(A.add0[item * A.add_item + size_t(i) * n + x], A.pfac[i],
-                                       A.pfac_s[i], m.q), m.q);
-            if (A.add1)
-                y1 = add_mod(y1, shoup(A.add1[item * A.add_item + size_t(i) * n + x], A.pfac[i],
-                                       A.pfac_s[i], m.q), m.q);
-        }
-        uint64_t *y = A.y + item * A.y_item;
-        y[size_t(i) * n + x] = y0;
-        y[(size_t(A.M) + i) * n + x] = y1;
+    uint64_t d0 = 0, d1 = 0;
+    if (fold) {
+        if (A.add0) d0 = A.add0[item * A.add_item + size_t(i) * n + x];
+        if (A.add1) d1 = A.add1[item * A.add_item + size_t(i) * n + x];
     }
+    U128 acc0{0, 0}, acc1{0, 0};
+#pragma unroll
+    for (int j = 0; j < BMAX; j++) {
+        if (uint32_t(j) < A.beta) {
+            mac(acc0, cj[j], kb[j]);
+            mac(acc1, cj[j], ka[j]);
+        }
+    }
+    uint64_t y0 = reduce128(acc0, m), y1 = reduce128(acc1, m);
+    if (fold) {
+        if (A.add0) y0 = add_mod(y0, shoup(d0, A.pfac[i], A.pfac_s[i], m.q), m.q);
+        if (A.add1) y1 = add_mod(y1, shoup(d1, A.pfac[i], A.pfac_s[i], m.q), m.q);
+    }
+    uint64_t *y = A.y + item * A.y_item;
+    y[size_t(i) * n + x] = y0;
+    y[(size_t(A.M) + i) * n + x] = y1;
 }
 
 int launch_ip(const Context &c, const IpArgs &a, uint32_t count, cudaStream_t s) {
-    const dim3 g = coeff_grid(c.n, a.M, 1);
+    const dim3 g(count, unsigned((c.n + 255) / 256), a.M);
     if (a.beta <= 4)
-        k_ip<4><<<g, 256, 0, s>>>(a, count, c.d_mods, c.log_n);
+        k_ip<4><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n);
     else if (a.beta <= 8)
-        k_ip<8><<<g, 256, 0, s>>>(a, count, c.d_mods, c.log_n);
+        k_ip<8><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n);
     else if (a.beta <= 16)
-        k_ip<16><<<g, 256, 0, s>>>(a, count, c.d_mods, c.log_n);
+        k_ip<16><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n);
     else
-        k_ip<32><<<g, 256, 0, s>>>(a, count, c.d_mods, c.log_n);
+        k_ip<32><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n);
     return ok();
 }
 

@@ -151,6 +151,19 @@ int launch_ntt_fwd(const Context &c, const uint64_t *src, uint64_t *dst, const L
 int launch_ntt_inv(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
                    uint32_t n_limbs, cudaStream_t s);
 
+// Forward NTT whose last pass also finishes the ModDown: for map entry r of
+// group g it writes out = (y - NTT(lift)) * dinv[r] (+ add) instead of the
+// transform (the lift itself is left in its column-pass state).
+struct NttEpilogue {
+    const uint64_t *y, *add;
+    uint64_t *out;
+    uint32_t y_stride, add_stride, out_stride;  // per group, in limbs
+    uint16_t y_off[kMapMax], add_off[kMapMax], out_off[kMapMax];
+    uint64_t dinv[kMapMax], dinv_s[kMapMax];
+};
+int launch_ntt_fwd_combine(const Context &c, uint64_t *lift, const LimbMap &map, uint32_t n_limbs,
+                           const NttEpilogue &epi, cudaStream_t s);
+
 // Exact base conversion (conv.cu): grid over (coefficient, item, plan).
 // grid.z runs plan z over items item = 0..items-1 (grid.y): sources at
 // src + item * src_item + src_off * N, targets at dst + item * dst_item + ...;

@@ -52,7 +52,7 @@ __device__ __forceinline__ uint64_t reduce4(uint64_t x, uint64_t q) {
 // ------------------------------------------------------------------ forward
 
 template <int LOGR, int LOGE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_ntt_fwd_cols(const uint64_t *src, uint64_t *dst, const LimbMap map,
                const DevMod *__restrict__ mods, const ulonglong2 *__restrict__ tw, int log_n) {
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CW = 256 / T;
@@ -102,10 +102,10 @@ k_ntt_fwd_cols(const uint64_t *src, uint64_t *dst, const LimbMap map,
     for (int v = 0; v < E; v++) out[c + size_t(tau * E + v) * S] = x[v];
 }
 
-template <int LOGR, int LOGE>
-__global__ void __launch_bounds__(256)
+template <int LOGR, int LOGE, bool EPI>
+__global__ void __launch_bounds__(256, 4)
 k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__restrict__ mods,
-               const ulonglong2 *__restrict__ tw, int log_n) {
+               const ulonglong2 *__restrict__ tw, int log_n, const NttEpilogue epi) {
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CC = 256 / T;
     constexpr int RP = R + R / E;
     __shared__ uint64_t sm[CC * RP];
@@ -155,15 +155,32 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
 #pragma unroll
     for (int v = 0; v < E; v++) s[PAD(tau * E + v)] = reduce4(x[v], q);
     __syncthreads();
+    if (!EPI) {
 #pragma unroll
-    for (int v = 0; v < E; v++) base[tau + T * v] = s[PAD(tau + T * v)];
+        for (int v = 0; v < E; v++) base[tau + T * v] = s[PAD(tau + T * v)];
+    } else {
+        // ModDown combine: out = (y - lift) * D^-1 (+ add), lift now in NTT form
+        const size_t off = h * R;
+        const uint64_t *yp = epi.y + (size_t(g) * epi.y_stride + epi.y_off[r]) * N + off;
+        uint64_t *op = epi.out + (size_t(g) * epi.out_stride + epi.out_off[r]) * N + off;
+        const uint64_t *ap =
+            epi.add ? epi.add + (size_t(g) * epi.add_stride + epi.add_off[r]) * N + off : nullptr;
+        const uint64_t dv = epi.dinv[r], dvs = epi.dinv_s[r];
+#pragma unroll
+        for (int v = 0; v < E; v++) {
+            const int u = tau + T * v;
+            uint64_t o = shoup(yp[u] + q - s[PAD(u)], dv, dvs, q);
+            if (ap) o = add_mod(o, ap[u], q);
+            op[u] = o;
+        }
+    }
 #undef PAD
 }
 
 // ------------------------------------------------------------------ inverse
 
 template <int LOGR, int LOGE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_ntt_inv_rows(const uint64_t *src, uint64_t *dst, const LimbMap map,
                const DevMod *__restrict__ mods, const ulonglong2 *__restrict__ tw, int log_n) {
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CC = 256 / T;
@@ -222,7 +239,7 @@ k_ntt_inv_rows(const uint64_t *src, uint64_t *dst, const LimbMap map,
 }
 
 template <int LOGR, int LOGE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_ntt_inv_cols(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__restrict__ mods,
                const ulonglong2 *__restrict__ tw, int log_n) {
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CW = 256 / T;
@@ -284,12 +301,16 @@ k_ntt_inv_cols(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
 
 template <int R1, int E1, int R2, int E2>
 static int run_fwd(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
-                   uint32_t n_limbs, cudaStream_t s) {
+                   uint32_t n_limbs, cudaStream_t s, const NttEpilogue *epi = nullptr) {
     const size_t N = c.n;
     dim3 g1(unsigned((N >> R1) / (256 / ((1 << R1) >> E1))), n_limbs);
     k_ntt_fwd_cols<R1, E1><<<g1, 256, 0, s>>>(src, dst, map, c.d_mods, c.d_twf, c.log_n);
     dim3 g2(unsigned((N >> R2) / (256 / ((1 << R2) >> E2))), n_limbs);
-    k_ntt_fwd_rows<R2, E2><<<g2, 256, 0, s>>>(dst, map, c.d_mods, c.d_twf, c.log_n);
+    if (epi)
+        k_ntt_fwd_rows<R2, E2, true><<<g2, 256, 0, s>>>(dst, map, c.d_mods, c.d_twf, c.log_n, *epi);
+    else
+        k_ntt_fwd_rows<R2, E2, false><<<g2, 256, 0, s>>>(dst, map, c.d_mods, c.d_twf, c.log_n,
+                                                         NttEpilogue{});
     note_launches(2);
     return cudaGetLastError() == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
 }
@@ -307,17 +328,27 @@ static int run_inv(const Context &c, const uint64_t *src, uint64_t *dst, const L
 }
 
 // (column pass log size, its LOGE, row pass log size, its LOGE) per log N
-int launch_ntt_fwd(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
-                   uint32_t n_limbs, cudaStream_t s) {
+static int fwd_dispatch(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
+                        uint32_t n_limbs, cudaStream_t s, const NttEpilogue *epi) {
     if (n_limbs == 0) return CATFHE_OK;
     switch (c.log_n) {
-        case 12: return run_fwd<6, 3, 6, 3>(c, src, dst, map, n_limbs, s);
-        case 13: return run_fwd<7, 4, 6, 3>(c, src, dst, map, n_limbs, s);
-        case 14: return run_fwd<7, 4, 7, 4>(c, src, dst, map, n_limbs, s);
-        case 15: return run_fwd<8, 4, 7, 4>(c, src, dst, map, n_limbs, s);
-        case 16: return run_fwd<8, 4, 8, 4>(c, src, dst, map, n_limbs, s);
+        case 12: return run_fwd<6, 3, 6, 3>(c, src, dst, map, n_limbs, s, epi);
+        case 13: return run_fwd<7, 4, 6, 3>(c, src, dst, map, n_limbs, s, epi);
+        case 14: return run_fwd<7, 4, 7, 4>(c, src, dst, map, n_limbs, s, epi);
+        case 15: return run_fwd<8, 4, 7, 4>(c, src, dst, map, n_limbs, s, epi);
+        case 16: return run_fwd<8, 4, 8, 4>(c, src, dst, map, n_limbs, s, epi);
         default: return CATFHE_EINVAL;
     }
+}
+
+int launch_ntt_fwd(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
+                   uint32_t n_limbs, cudaStream_t s) {
+    return fwd_dispatch(c, src, dst, map, n_limbs, s, nullptr);
+}
+
+int launch_ntt_fwd_combine(const Context &c, uint64_t *lift, const LimbMap &map, uint32_t n_limbs,
+                           const NttEpilogue &epi, cudaStream_t s) {
+    return fwd_dispatch(c, lift, lift, map, n_limbs, s, &epi);
 }
 
 int launch_ntt_inv(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,

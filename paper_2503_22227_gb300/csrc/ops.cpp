@@ -223,9 +223,39 @@ static int moddown(Context &c, uint64_t *y, uint64_t *lift, uint64_t *out, const
     PlanList pl;
     TRY(make_list(c, {{"moddown/" + std::to_string(level) + (fused ? "/f" : ""), sp}}, pl));
     TRY(launch_conv(c, pl, y, size_t(M) * n, 0, lift, size_t(lo) * n, 0, 2 * count, s));
+    // D^-1 mod q_i, D = P (fused: P q_{l-1})
+    std::vector<uint64_t> dinv(lo), dinv_s(lo);
+    for (int i = 0; i < lo; i++) {
+        const uint64_t q = c.mod(i);
+        uint64_t D = pmod(c, q);
+        if (fused) D = h_mulmod(D, c.mod(level - 1) % q, q);
+        dinv[i] = h_invmod(D, q);
+        dinv_s[i] = h_shoup(dinv[i], q);
+    }
     if (ntt_form) {
-        LimbMap m = map_identity(uint32_t(lo));
-        TRY(launch_ntt_fwd(c, lift, lift, m, uint32_t(2 * lo) * count, s));
+        // NTT of the lift whose last pass writes (y - lift) D^-1 straight to out
+        LimbMap m{};
+        NttEpilogue e{};
+        m.period = uint32_t(2 * lo);
+        m.src_stride = m.dst_stride = uint32_t(2 * lo);
+        e.y = y;
+        e.add = add;
+        e.out = out;
+        e.y_stride = uint32_t(2 * M);
+        e.add_stride = uint32_t(2 * lo);
+        e.out_stride = uint32_t(2 * lo);
+        for (int p = 0; p < 2; p++)
+            for (int i = 0; i < lo; i++) {
+                const int r = p * lo + i;
+                m.src_off[r] = m.dst_off[r] = uint16_t(r);
+                m.prime[r] = uint8_t(i);
+                e.y_off[r] = uint16_t(p * M + i);
+                e.add_off[r] = uint16_t(r);
+                e.out_off[r] = uint16_t(r);
+                e.dinv[r] = dinv[i];
+                e.dinv_s[r] = dinv_s[i];
+            }
+        return launch_ntt_fwd_combine(c, lift, m, uint32_t(2 * lo) * count, e, s);
     }
     CombineArgs a{};
     a.y = y;
@@ -242,12 +272,9 @@ static int moddown(Context &c, uint64_t *y, uint64_t *lift, uint64_t *out, const
     a.out_poly = size_t(lo) * n;
     a.lo = uint32_t(lo);
     for (int i = 0; i < lo; i++) {
-        const uint64_t q = c.mod(i);
-        uint64_t D = pmod(c, q);
-        if (fused) D = h_mulmod(D, c.mod(level - 1) % q, q);
         a.prime[i] = uint8_t(i);
-        a.dinv[i] = h_invmod(D, q);
-        a.dinv_s[i] = h_shoup(a.dinv[i], q);
+        a.dinv[i] = dinv[i];
+        a.dinv_s[i] = dinv_s[i];
     }
     return launch_combine(c, a, count, s);
 }
@@ -601,25 +628,26 @@ int op_rescale(Context &c, const uint64_t *a, uint64_t *out, uint32_t level, uin
     PlanList pl;
     TRY(make_list(c, {{"rescale/" + std::to_string(lvl), sp}}, pl));
     TRY(launch_conv(c, pl, last, n, 0, lift, size_t(lo) * n, 0, 2 * count, s));
-    LimbMap ml = map_identity(uint32_t(lo));
-    TRY(launch_ntt_fwd(c, lift, lift, ml, uint32_t(2 * lo) * count, s));
-    CombineArgs ca{};
-    ca.y = a;
-    ca.lift = lift;
-    ca.out = out;
-    ca.y_item = size_t(2) * lvl * n;
-    ca.y_poly = size_t(lvl) * n;
-    ca.lift_item = size_t(2) * lo * n;
-    ca.lift_poly = size_t(lo) * n;
-    ca.out_item = size_t(2) * lo * n;
-    ca.out_poly = size_t(lo) * n;
-    ca.lo = uint32_t(lo);
-    for (int i = 0; i < lo; i++) {
-        ca.prime[i] = uint8_t(i);
-        ca.dinv[i] = h_invmod(c.mod(lvl - 1) % c.mod(i), c.mod(i));
-        ca.dinv_s[i] = h_shoup(ca.dinv[i], c.mod(i));
-    }
-    return launch_combine(c, ca, count, s);
+    // NTT of the lift, its last pass writing (a - lift) q_{l-1}^-1 to out
+    LimbMap m2{};
+    NttEpilogue e{};
+    m2.period = uint32_t(2 * lo);
+    m2.src_stride = m2.dst_stride = uint32_t(2 * lo);
+    e.y = a;
+    e.out = out;
+    e.y_stride = uint32_t(2 * lvl);
+    e.out_stride = uint32_t(2 * lo);
+    for (int p = 0; p < 2; p++)
+        for (int i = 0; i < lo; i++) {
+            const int r = p * lo + i;
+            m2.src_off[r] = m2.dst_off[r] = uint16_t(r);
+            m2.prime[r] = uint8_t(i);
+            e.y_off[r] = uint16_t(p * lvl + i);
+            e.out_off[r] = uint16_t(r);
+            e.dinv[r] = h_invmod(c.mod(lvl - 1) % c.mod(i), c.mod(i));
+            e.dinv_s[r] = h_shoup(e.dinv[r], c.mod(i));
+        }
+    return launch_ntt_fwd_combine(c, lift, m2, uint32_t(2 * lo) * count, e, s);
 }
 
 int op_add(Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t level,
