@@ -106,6 +106,9 @@ int ctx_init(Context &c, const catfhe_params &p) {
         for (uint64_t q : used)
             if (q % c.t == 0 || h_invmod(q % c.t, c.t) == 0) return CATFHE_EINVAL;
     }
+    // the key-switching inner product sums beta + 1 products below 2^64 q
+    for (uint64_t q : used)
+        if ((u128)(c.beta + 1) * q >= ((u128)1 << 64)) return CATFHE_EINVAL;
     for (uint64_t q : used) c.primes.push_back(HostPrime{q, h_min_psi(q, c.log_n)});
     const size_t np = c.primes.size(), n = c.n;
     for (auto &hp : c.primes) c.hmods.push_back(h_devmod(hp.q, n, hp.psi));

@@ -168,12 +168,6 @@ __device__ __forceinline__ MontView mont_view(const uint64_t *p) {
     return v;
 }
 
-// Montgomery reduction of acc < 2^64 p: acc 2^-64 mod p, in [0, 2p).
-__device__ __forceinline__ uint64_t redc(U128 acc, uint64_t p, uint64_t pinv) {
-    const uint64_t u = acc.lo * pinv;
-    return acc.hi + mulhi(u, p) + (acc.lo != 0 ? 1 : 0);
-}
-
 template <int KMAX>
 __device__ __forceinline__ bool mixed_radix_mont(uint64_t (&a)[KMAX], const MontView &P) {
 #pragma unroll(KMAX <= 16 ? KMAX : 1)

@@ -73,13 +73,12 @@ k_ip(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
             ka[j] = A.key[((size_t(j) * 2 + 1) * KL + A.key_limb[i]) * n + x];
         }
     }
-    const bool fold = i < A.level && A.pfac[i] != 0;
-    uint64_t d0 = 0, d1 = 0;
-    if (fold) {
-        if (A.add0) d0 = A.add0[item * A.add_item + size_t(i) * n + x];
-        if (A.add1) d1 = A.add1[item * A.add_item + size_t(i) * n + x];
-    }
+    // keys (and P) are in Montgomery form: one reduction per sum
     U128 acc0{0, 0}, acc1{0, 0};
+    if (i < A.level && A.pfac[i] != 0) {
+        if (A.add0) mac(acc0, A.add0[item * A.add_item + size_t(i) * n + x], A.pfac[i]);
+        if (A.add1) mac(acc1, A.add1[item * A.add_item + size_t(i) * n + x], A.pfac[i]);
+    }
 #pragma unroll
     for (int j = 0; j < BMAX; j++) {
         if (uint32_t(j) < A.beta) {
@@ -87,11 +86,8 @@ k_ip(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
             mac(acc1, cj[j], ka[j]);
         }
     }
-    uint64_t y0 = reduce128(acc0, m), y1 = reduce128(acc1, m);
-    if (fold) {
-        if (A.add0) y0 = add_mod(y0, shoup(d0, A.pfac[i], A.pfac_s[i], m.q), m.q);
-        if (A.add1) y1 = add_mod(y1, shoup(d1, A.pfac[i], A.pfac_s[i], m.q), m.q);
-    }
+    const uint64_t y0 = csub(redc(acc0, m.q, m.qinv), m.q);
+    const uint64_t y1 = csub(redc(acc1, m.q, m.qinv), m.q);
     uint64_t *y = A.y + item * A.y_item;
     y[size_t(i) * n + x] = y0;
     y[(size_t(A.M) + i) * n + x] = y1;
@@ -284,6 +280,24 @@ k_ksk_row(const uint64_t *__restrict__ a, const uint64_t *__restrict__ sk,
     uint64_t v = sub_mod(e[o], mul_mod(a[o], sk[o], m), m.q);
     if (pfac[i]) v = add_mod(v, shoup(sp[o], pfac[i], pfac_s[i], m.q), m.q);
     b[o] = v;
+}
+
+__global__ void __launch_bounds__(256)
+k_scale_limbs(uint64_t *x, uint32_t limbs, const uint64_t *__restrict__ w,
+              const uint64_t *__restrict__ w_s, const DevMod *__restrict__ mods, uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t j = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const uint32_t i = blockIdx.y % limbs;
+    uint64_t *p = x + size_t(blockIdx.y) * n + j;
+    *p = shoup(*p, w[i], w_s[i], mods[i].q);
+}
+
+int launch_scale_limbs(const Context &c, uint64_t *x, uint32_t limbs, uint32_t groups,
+                       const uint64_t *w, const uint64_t *w_s, cudaStream_t s) {
+    k_scale_limbs<<<coeff_grid(c.n, limbs * groups), 256, 0, s>>>(x, limbs, w, w_s, c.d_mods,
+                                                                c.log_n);
+    return ok();
 }
 
 int launch_ksk_row(const Context &c, const uint64_t *a, const uint64_t *sk, const uint64_t *e,

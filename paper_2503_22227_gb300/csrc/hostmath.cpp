@@ -110,6 +110,9 @@ DevMod h_devmod(uint64_t q, uint64_t n, uint64_t psi) {
     m.r64 = (uint64_t)(((u128)1 << 64) % q);
     m.r64_s = h_shoup(m.r64, q);
     m.one_s = h_shoup(1, q);
+    uint64_t x = q;  // -q^-1 mod 2^64 by Newton's iteration (q odd)
+    for (int i = 0; i < 6; i++) x *= 2 - q * x;
+    m.qinv = 0 - x;
     if (n) {
         m.ninv = h_invmod(n % q, q);
         m.ninv_s = h_shoup(m.ninv, q);

@@ -25,6 +25,8 @@ struct DevMod {
     uint64_t one_s;           // floor(2^64 / q): Shoup quotient of 1
     uint64_t ninv, ninv_s;    // N^-1 mod q
     uint64_t ninvw, ninvw_s;  // N^-1 * psi^-1(bitrev 1) mod q (last inverse stage)
+    uint64_t qinv;            // -q^-1 mod 2^64 (Montgomery reduction)
+    uint64_t pad;
 };
 
 // Addressing of a batch of limbs: limb l of a launch is entry r = l % period
@@ -137,7 +139,9 @@ struct Keys {
     uint8_t seed[32];
     uint64_t *s_ntt = nullptr;                 // [L+K][N] NTT form
     uint64_t *pk = nullptr;                    // [2][L][N] NTT form
-    std::map<uint64_t, uint64_t *> ksk;        // id -> [beta][2][L+K][N] NTT form
+    // id -> [beta][2][L+K][N], NTT form and Montgomery form (times 2^64 mod
+    // the limb's prime), so the inner product needs one reduction per sum
+    std::map<uint64_t, uint64_t *> ksk;
 };
 
 // Number of kernels this library has launched (all contexts, all threads).
@@ -193,7 +197,7 @@ int launch_tensor(const Context &c, const TensorArgs &a, uint32_t count, cudaStr
 struct IpArgs {
     const uint64_t *ext;       // [count][beta][M][N]: lifted digits (NTT form)
     const uint64_t *own;       // [count][l][N]: d2 in NTT form (digit's own limbs), or null
-    const uint64_t *key;       // [beta_L][2][L+K][N]
+    const uint64_t *key;       // [beta_L][2][L+K][N], Montgomery form
     const uint64_t *add0, *add1;  // [count][l][N] added times P (Q positions), or null
     uint64_t *y;               // [count][2][M][N]
     size_t ext_item, own_item, add_item, y_item;
@@ -201,7 +205,7 @@ struct IpArgs {
     uint32_t alpha;
     uint8_t prime[kMapMax];    // prime of position i
     uint16_t key_limb[kMapMax];
-    uint64_t pfac[kMapMax], pfac_s[kMapMax];  // P mod prime(i) (0 for P positions)
+    uint64_t pfac[kMapMax];    // P 2^64 mod prime(i) (0 for P positions)
 };
 int launch_ip(const Context &c, const IpArgs &a, uint32_t count, cudaStream_t s);
 
@@ -254,6 +258,10 @@ int launch_pointwise(const Context &c, const uint64_t *a, const uint64_t *b, uin
 int launch_ksk_row(const Context &c, const uint64_t *a, const uint64_t *sk, const uint64_t *e,
                    const uint64_t *sp, uint64_t *b, uint32_t limbs, const uint64_t *pfac,
                    const uint64_t *pfac_s, cudaStream_t s);
+// x[g][i] *= w_i (Shoup constants per limb i of a group of `limbs`), groups of
+// `limbs` consecutive limbs, limb i mod prime i.
+int launch_scale_limbs(const Context &c, uint64_t *x, uint32_t limbs, uint32_t groups,
+                       const uint64_t *w, const uint64_t *w_s, cudaStream_t s);
 
 // host math (hostmath.cpp)
 uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t m);

@@ -54,6 +54,13 @@ __device__ __forceinline__ uint64_t reduce128(U128 x, const DevMod &m) {
     return csub(r, m.q);
 }
 
+// Montgomery reduction of acc < 2^64 q: acc 2^-64 mod q, in [0, 2q)
+// (u = lo (-q^-1) mod 2^64 makes acc + u q divisible by 2^64).
+__device__ __forceinline__ uint64_t redc(U128 acc, uint64_t q, uint64_t qinv) {
+    const uint64_t u = acc.lo * qinv;
+    return acc.hi + mulhi(u, q) + (acc.lo != 0 ? 1 : 0);
+}
+
 // a*b mod q for a, b < 2^64 (exact).
 __device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, const DevMod &m) {
     U128 x{a * b, mulhi(a, b)};

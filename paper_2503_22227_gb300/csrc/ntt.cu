@@ -49,10 +49,67 @@ __device__ __forceinline__ uint64_t reduce4(uint64_t x, uint64_t q) {
     return csub(csub(x, 2 * q), q);
 }
 
+// Forward butterfly without any conditional subtraction, for q < 2^58: the
+// bound grows by 2q per stage, from < 4q to < 36q after 16 stages, which a
+// 64-bit word still holds; the last pass reduces fully.
+__device__ __forceinline__ void ct_bfly_wide(uint64_t &a, uint64_t &b, ulonglong2 w, uint64_t q) {
+    const uint64_t t = shoup_lazy(b, w.x, w.y, q);   // [0, 2q)
+    const uint64_t a0 = a;
+    a = a0 + t;
+    b = a0 + 2 * q - t;
+}
+
+template <bool WIDE>
+__device__ __forceinline__ void fwd_bfly(uint64_t &a, uint64_t &b, ulonglong2 w, uint64_t q) {
+    if (WIDE)
+        ct_bfly_wide(a, b, w, q);
+    else
+        ct_bfly(a, b, w, q);
+}
+
+// Any word below 2^64 -> [0, q) (Shoup product by 1, then one subtraction).
+__device__ __forceinline__ uint64_t reduce_any(uint64_t x, const DevMod &m) {
+    return csub(shoup_lazy(x, 1, m.one_s, m.q), m.q);
+}
+
+constexpr uint64_t kWideBound = uint64_t(1) << 58;
+
 // ------------------------------------------------------------------ forward
 
+template <int LOGR, int LOGE, bool WIDE>
+__device__ __forceinline__ void fwd_cols_body(uint64_t (&x)[1 << LOGE], uint64_t *sm,
+                                              const ulonglong2 *w, uint64_t q, int cl, int tau) {
+    constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CW = 256 / T;
+    // stages 0 .. LOGE-1: partners at distance T*half are in this thread
+#pragma unroll
+    for (int st = 0; st < LOGE; st++) {
+        const int half = E >> (st + 1);
+#pragma unroll
+        for (int v = 0; v < E; v++) {
+            if (v & half) continue;
+            fwd_bfly<WIDE>(x[v], x[v + half], w[(1 << st) + (v >> (LOGE - st))], q);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < E; v++) sm[(tau + T * v) * CW + cl] = x[v];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < E; v++) x[v] = sm[(tau * E + v) * CW + cl];
+    // stages LOGE .. LOGR-1: partners at distance < E
+#pragma unroll
+    for (int st = LOGE; st < LOGR; st++) {
+        const int dist = 1 << (LOGR - 1 - st);
+#pragma unroll
+        for (int v = 0; v < E; v++) {
+            if (v & dist) continue;
+            const int rr = tau * E + v;
+            fwd_bfly<WIDE>(x[v], x[v + dist], w[(1 << st) + (rr >> (LOGR - st))], q);
+        }
+    }
+}
+
 template <int LOGR, int LOGE>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256)
 k_ntt_fwd_cols(const uint64_t *src, uint64_t *dst, const LimbMap map,
                const DevMod *__restrict__ mods, const ulonglong2 *__restrict__ tw, int log_n) {
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CW = 256 / T;
@@ -72,60 +129,20 @@ k_ntt_fwd_cols(const uint64_t *src, uint64_t *dst, const LimbMap map,
     uint64_t x[E];
 #pragma unroll
     for (int v = 0; v < E; v++) x[v] = in[c + size_t(tau + T * v) * S];
-    // stages 0 .. LOGE-1: partners at distance T*half are in this thread
-#pragma unroll
-    for (int st = 0; st < LOGE; st++) {
-        const int half = E >> (st + 1);
-#pragma unroll
-        for (int v = 0; v < E; v++) {
-            if (v & half) continue;
-            ct_bfly(x[v], x[v + half], w[(1 << st) + (v >> (LOGE - st))], q);
-        }
-    }
-#pragma unroll
-    for (int v = 0; v < E; v++) sm[(tau + T * v) * CW + cl] = x[v];
-    __syncthreads();
-#pragma unroll
-    for (int v = 0; v < E; v++) x[v] = sm[(tau * E + v) * CW + cl];
-    // stages LOGE .. LOGR-1: partners at distance < E
-#pragma unroll
-    for (int st = LOGE; st < LOGR; st++) {
-        const int dist = 1 << (LOGR - 1 - st);
-#pragma unroll
-        for (int v = 0; v < E; v++) {
-            if (v & dist) continue;
-            const int rr = tau * E + v;
-            ct_bfly(x[v], x[v + dist], w[(1 << st) + (rr >> (LOGR - st))], q);
-        }
-    }
+    if (q < kWideBound)
+        fwd_cols_body<LOGR, LOGE, true>(x, sm, w, q, cl, tau);
+    else
+        fwd_cols_body<LOGR, LOGE, false>(x, sm, w, q, cl, tau);
 #pragma unroll
     for (int v = 0; v < E; v++) out[c + size_t(tau * E + v) * S] = x[v];
 }
 
-template <int LOGR, int LOGE, bool EPI>
-__global__ void __launch_bounds__(256, 4)
-k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__restrict__ mods,
-               const ulonglong2 *__restrict__ tw, int log_n, const NttEpilogue epi) {
-    constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CC = 256 / T;
-    constexpr int RP = R + R / E;
-    __shared__ uint64_t sm[CC * RP];
-    const uint32_t limb = blockIdx.y;
-    const uint32_t g = limb / map.period, r = limb % map.period;
-    const size_t N = size_t(1) << log_n;
-    uint64_t *out = data + (size_t(g) * map.dst_stride + map.dst_off[r]) * N;
-    const int p = map.prime[r];
-    const uint64_t q = mods[p].q;
-    const ulonglong2 *w = tw + size_t(p) * N;
-    const int k1 = log_n - LOGR;
-    const int chl = threadIdx.x / T, tau = threadIdx.x % T;
-    const size_t h = size_t(blockIdx.x) * CC + chl;
-    uint64_t *base = out + h * R;
-    uint64_t *s = sm + chl * RP;
+template <int LOGR, int LOGE, bool WIDE>
+__device__ __forceinline__ void fwd_rows_body(uint64_t (&x)[1 << LOGE], uint64_t *s,
+                                              const ulonglong2 *w, uint64_t q, int k1, size_t h,
+                                              int tau) {
+    constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E;
 #define PAD(u) ((u) + ((u) >> LOGE))
-
-    uint64_t x[E];
-#pragma unroll
-    for (int v = 0; v < E; v++) x[v] = base[tau + T * v];
 #pragma unroll
     for (int st = 0; st < LOGE; st++) {
         const int half = E >> (st + 1);
@@ -133,7 +150,7 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
         for (int v = 0; v < E; v++) {
             if (v & half) continue;
             const size_t idx = (size_t(1) << (k1 + st)) + (h << st) + (v >> (LOGE - st));
-            ct_bfly(x[v], x[v + half], w[idx], q);
+            fwd_bfly<WIDE>(x[v], x[v + half], w[idx], q);
         }
     }
 #pragma unroll
@@ -149,11 +166,44 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
             if (v & dist) continue;
             const int u = tau * E + v;
             const size_t idx = (size_t(1) << (k1 + st)) + (h << st) + (u >> (LOGR - st));
-            ct_bfly(x[v], x[v + dist], w[idx], q);
+            fwd_bfly<WIDE>(x[v], x[v + dist], w[idx], q);
         }
     }
+#undef PAD
+}
+
+template <int LOGR, int LOGE, bool EPI>
+__global__ void __launch_bounds__(256)
+k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__restrict__ mods,
+               const ulonglong2 *__restrict__ tw, int log_n, const NttEpilogue epi) {
+    constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CC = 256 / T;
+    constexpr int RP = R + R / E;
+    __shared__ uint64_t sm[CC * RP];
+    const uint32_t limb = blockIdx.y;
+    const uint32_t g = limb / map.period, r = limb % map.period;
+    const size_t N = size_t(1) << log_n;
+    uint64_t *out = data + (size_t(g) * map.dst_stride + map.dst_off[r]) * N;
+    const int p = map.prime[r];
+    const DevMod m = mods[p];
+    const uint64_t q = m.q;
+    const ulonglong2 *w = tw + size_t(p) * N;
+    const int k1 = log_n - LOGR;
+    const int chl = threadIdx.x / T, tau = threadIdx.x % T;
+    const size_t h = size_t(blockIdx.x) * CC + chl;
+    uint64_t *base = out + h * R;
+    uint64_t *s = sm + chl * RP;
+#define PAD(u) ((u) + ((u) >> LOGE))
+
+    uint64_t x[E];
 #pragma unroll
-    for (int v = 0; v < E; v++) s[PAD(tau * E + v)] = reduce4(x[v], q);
+    for (int v = 0; v < E; v++) x[v] = base[tau + T * v];
+    const bool wide = q < kWideBound;
+    if (wide)
+        fwd_rows_body<LOGR, LOGE, true>(x, s, w, q, k1, h, tau);
+    else
+        fwd_rows_body<LOGR, LOGE, false>(x, s, w, q, k1, h, tau);
+#pragma unroll
+    for (int v = 0; v < E; v++) s[PAD(tau * E + v)] = wide ? reduce_any(x[v], m) : reduce4(x[v], q);
     __syncthreads();
     if (!EPI) {
 #pragma unroll
@@ -180,7 +230,7 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
 // ------------------------------------------------------------------ inverse
 
 template <int LOGR, int LOGE>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256)
 k_ntt_inv_rows(const uint64_t *src, uint64_t *dst, const LimbMap map,
                const DevMod *__restrict__ mods, const ulonglong2 *__restrict__ tw, int log_n) {
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CC = 256 / T;
@@ -239,7 +289,7 @@ k_ntt_inv_rows(const uint64_t *src, uint64_t *dst, const LimbMap map,
 }
 
 template <int LOGR, int LOGE>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256)
 k_ntt_inv_cols(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__restrict__ mods,
                const ulonglong2 *__restrict__ tw, int log_n) {
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CW = 256 / T;

@@ -176,8 +176,8 @@ static int inner_product(Context &c, const uint64_t *ext, const uint64_t *own, c
         a.prime[i] = uint8_t(gp);
         a.key_limb[i] = uint16_t(gp);
         if (i < level) {
-            a.pfac[i] = pmod(c, c.mod(i));
-            a.pfac_s[i] = h_shoup(a.pfac[i], c.mod(i));
+            const uint64_t q = c.mod(i), r = (uint64_t)(((unsigned __int128)1 << 64) % q);
+            a.pfac[i] = h_mulmod(pmod(c, q), r, q);  // P in Montgomery form
         }
     }
     return launch_ip(c, a, count, s);
@@ -746,6 +746,15 @@ static int gen_ksk(Context &c, Keys &k, uint64_t id, const uint64_t *sp, cudaStr
         if (!rc) rc = launch_ksk_row(c, aj, k.s_ntt, e, sp, bj, uint32_t(E), pfc.v, pfc.s, s);
         if (!rc) rc = cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
     }
+    // Montgomery form: every limb times 2^64 mod its prime
+    if (!rc) {
+        std::vector<uint64_t> rv(E);
+        for (int i = 0; i < E; i++) rv[i] = (uint64_t)(((unsigned __int128)1 << 64) % mods[i]);
+        DevConst rm;
+        rc = rm.set(rv, mods);
+        if (!rc) rc = launch_scale_limbs(c, key, uint32_t(E), uint32_t(c.beta * 2), rm.v, rm.s, s);
+        if (!rc) rc = cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
+    }
     cudaFree(e);
     if (rc) {
         cudaFree(key);
@@ -858,6 +867,15 @@ int op_keys_export(Context &c, const Keys &k, uint64_t id, int64_t *s_out, uint6
         auto it = k.ksk.find(id);
         if (it == k.ksk.end()) rc = CATFHE_ENOKEY;
         if (!rc) rc = launch_ntt_inv(c, it->second, tmp, mE, uint32_t(c.beta * 2 * E), 0);
+        // undo the Montgomery form: times 2^-64 mod each prime
+        std::vector<uint64_t> rv(E), mods(E);
+        for (int i = 0; i < E && !rc; i++) {
+            mods[i] = c.mod(i);
+            rv[i] = h_invmod((uint64_t)(((unsigned __int128)1 << 64) % mods[i]), mods[i]);
+        }
+        DevConst ri;
+        if (!rc) rc = ri.set(rv, mods);
+        if (!rc) rc = launch_scale_limbs(c, tmp, uint32_t(E), uint32_t(c.beta * 2), ri.v, ri.s, 0);
         if (!rc && cudaMemcpy(ksk_out, tmp, need * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
             rc = CATFHE_ECUDA;
     }
