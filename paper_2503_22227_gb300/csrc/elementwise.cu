@@ -21,27 +21,37 @@ static inline dim3 coeff_grid(size_t n, uint32_t y, uint32_t z = 1) {
 
 // ------------------------------------------------------------------ tensor
 
+__device__ __forceinline__ ulonglong2 ld2(const uint64_t *p) {
+    return *reinterpret_cast<const ulonglong2 *>(p);
+}
+__device__ __forceinline__ void st2(uint64_t *p, uint64_t a, uint64_t b) {
+    *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(a, b);
+}
+
+// Two adjacent coefficients per thread (16-byte loads and stores).
 __global__ void __launch_bounds__(256)
 k_tensor(const TensorArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
     const size_t n = size_t(1) << log_n;
-    const size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t x = 2 * (size_t(blockIdx.x) * blockDim.x + threadIdx.x);
     const uint32_t i = blockIdx.y, item = blockIdx.z;
     if (x >= n) return;
     const DevMod m = mods[A.prime[i]];
     const uint64_t *a = A.a + item * A.in_item, *b = A.b + item * A.in_item;
     const size_t l0 = size_t(i) * n + x, l1 = (size_t(A.limbs) + i) * n + x;
-    const uint64_t a0 = a[l0], a1 = a[l1], b0 = b[l0], b1 = b[l1];
+    const ulonglong2 a0 = ld2(a + l0), a1 = ld2(a + l1), b0 = ld2(b + l0), b1 = ld2(b + l1);
     const size_t o = item * A.out_item + size_t(i) * n + x;
-    A.d0[o] = mul_mod(a0, b0, m);
-    U128 acc{0, 0};
-    mac(acc, a0, b1);
-    mac(acc, a1, b0);
-    A.d1[o] = reduce128(acc, m);
-    A.d2[o] = mul_mod(a1, b1, m);
+    st2(A.d0 + o, mul_mod(a0.x, b0.x, m), mul_mod(a0.y, b0.y, m));
+    U128 s0{0, 0}, s1{0, 0};
+    mac(s0, a0.x, b1.x);
+    mac(s0, a1.x, b0.x);
+    mac(s1, a0.y, b1.y);
+    mac(s1, a1.y, b0.y);
+    st2(A.d1 + o, reduce128(s0, m), reduce128(s1, m));
+    st2(A.d2 + o, mul_mod(a1.x, b1.x, m), mul_mod(a1.y, b1.y, m));
 }
 
 int launch_tensor(const Context &c, const TensorArgs &a, uint32_t count, cudaStream_t s) {
-    k_tensor<<<coeff_grid(c.n, a.limbs, count), 256, 0, s>>>(a, c.d_mods, c.log_n);
+    k_tensor<<<coeff_grid(c.n / 2, a.limbs, count), 256, 0, s>>>(a, c.d_mods, c.log_n);
     return ok();
 }
 
@@ -56,45 +66,49 @@ __global__ void __launch_bounds__(256)
 k_ip(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
     const size_t n = size_t(1) << log_n;
     const uint32_t item = blockIdx.x, i = blockIdx.z;
-    const size_t x = size_t(blockIdx.y) * blockDim.x + threadIdx.x;
+    const size_t x = 2 * (size_t(blockIdx.y) * blockDim.x + threadIdx.x);
     if (x >= n) return;
     const DevMod m = mods[A.prime[i]];
     const uint32_t KL = A.L + A.K;
     const bool own_here = A.own != nullptr && i < A.level;
     const uint32_t own_digit = own_here ? i / A.alpha : 0xffffffffu;
     const uint64_t *ext = A.ext + item * A.ext_item;
-    uint64_t cj[BMAX], kb[BMAX], ka[BMAX];
-#pragma unroll
-    for (int j = 0; j < BMAX; j++) {
-        if (uint32_t(j) < A.beta) {
-            cj[j] = (uint32_t(j) == own_digit) ? A.own[item * A.own_item + size_t(i) * n + x]
-                                               : ext[(size_t(j) * A.M + i) * n + x];
-            kb[j] = A.key[((size_t(j) * 2 + 0) * KL + A.key_limb[i]) * n + x];
-            ka[j] = A.key[((size_t(j) * 2 + 1) * KL + A.key_limb[i]) * n + x];
-        }
-    }
     // keys (and P) are in Montgomery form: one reduction per sum
-    U128 acc0{0, 0}, acc1{0, 0};
+    U128 a0{0, 0}, a1{0, 0}, b0{0, 0}, b1{0, 0};
     if (i < A.level && A.pfac[i] != 0) {
-        if (A.add0) mac(acc0, A.add0[item * A.add_item + size_t(i) * n + x], A.pfac[i]);
-        if (A.add1) mac(acc1, A.add1[item * A.add_item + size_t(i) * n + x], A.pfac[i]);
+        if (A.add0) {
+            const ulonglong2 d = ld2(A.add0 + item * A.add_item + size_t(i) * n + x);
+            mac(a0, d.x, A.pfac[i]);
+            mac(a1, d.y, A.pfac[i]);
+        }
+        if (A.add1) {
+            const ulonglong2 d = ld2(A.add1 + item * A.add_item + size_t(i) * n + x);
+            mac(b0, d.x, A.pfac[i]);
+            mac(b1, d.y, A.pfac[i]);
+        }
     }
 #pragma unroll
     for (int j = 0; j < BMAX; j++) {
         if (uint32_t(j) < A.beta) {
-            mac(acc0, cj[j], kb[j]);
-            mac(acc1, cj[j], ka[j]);
+            const ulonglong2 c = (uint32_t(j) == own_digit)
+                                     ? ld2(A.own + item * A.own_item + size_t(i) * n + x)
+                                     : ld2(ext + (size_t(j) * A.M + i) * n + x);
+            const ulonglong2 kb = ld2(A.key + ((size_t(j) * 2 + 0) * KL + A.key_limb[i]) * n + x);
+            const ulonglong2 ka = ld2(A.key + ((size_t(j) * 2 + 1) * KL + A.key_limb[i]) * n + x);
+            mac(a0, c.x, kb.x);
+            mac(a1, c.y, kb.y);
+            mac(b0, c.x, ka.x);
+            mac(b1, c.y, ka.y);
         }
     }
-    const uint64_t y0 = csub(redc(acc0, m.q, m.qinv), m.q);
-    const uint64_t y1 = csub(redc(acc1, m.q, m.qinv), m.q);
     uint64_t *y = A.y + item * A.y_item;
-    y[size_t(i) * n + x] = y0;
-    y[(size_t(A.M) + i) * n + x] = y1;
+    st2(y + size_t(i) * n + x, csub(redc(a0, m.q, m.qinv), m.q), csub(redc(a1, m.q, m.qinv), m.q));
+    st2(y + (size_t(A.M) + i) * n + x, csub(redc(b0, m.q, m.qinv), m.q),
+        csub(redc(b1, m.q, m.qinv), m.q));
 }
 
 int launch_ip(const Context &c, const IpArgs &a, uint32_t count, cudaStream_t s) {
-    const dim3 g(count, unsigned((c.n + 255) / 256), a.M);
+    const dim3 g(count, unsigned((c.n / 2 + 255) / 256), a.M);
     if (a.beta <= 4)
         k_ip<4><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n);
     else if (a.beta <= 8)

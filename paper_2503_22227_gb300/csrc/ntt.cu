@@ -109,7 +109,7 @@ __device__ __forceinline__ void fwd_cols_body(uint64_t (&x)[1 << LOGE], uint64_t
 }
 
 template <int LOGR, int LOGE>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256)
 k_ntt_fwd_cols(const uint64_t *src, uint64_t *dst, const LimbMap map,
                const DevMod *__restrict__ mods, const ulonglong2 *__restrict__ tw, int log_n) {
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CW = 256 / T;
@@ -129,15 +129,12 @@ k_ntt_fwd_cols(const uint64_t *src, uint64_t *dst, const LimbMap map,
     uint64_t x[E];
 #pragma unroll
     for (int v = 0; v < E; v++) x[v] = in[c + size_t(tau + T * v) * S];
-    if (q < kWideBound) {
+    // q < 2^58: no conditional subtractions; words leave below 4q + 2 LOGR q
+    // and the row pass reduces them on load
+    if (q < kWideBound)
         fwd_cols_body<LOGR, LOGE, true>(x, sm, w, q, cl, tau);
-        // words grew to < 4q + 2 LOGR q: back to [0, q) for the row pass
-        const DevMod m = mods[p];
-#pragma unroll
-        for (int v = 0; v < E; v++) x[v] = reduce_any(x[v], m);
-    } else {
+    else
         fwd_cols_body<LOGR, LOGE, false>(x, sm, w, q, cl, tau);
-    }
 #pragma unroll
     for (int v = 0; v < E; v++) out[c + size_t(tau * E + v) * S] = x[v];
 }
@@ -178,7 +175,7 @@ __device__ __forceinline__ void fwd_rows_body(uint64_t (&x)[1 << LOGE], uint64_t
 }
 
 template <int LOGR, int LOGE, bool EPI>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
 k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__restrict__ mods,
                const ulonglong2 *__restrict__ tw, int log_n, const NttEpilogue epi) {
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CC = 256 / T;
@@ -202,6 +199,10 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
     uint64_t x[E];
 #pragma unroll
     for (int v = 0; v < E; v++) x[v] = base[tau + T * v];
+    if (q < kWideBound) {  // the column pass left words below 2^64, not 4q
+#pragma unroll
+        for (int v = 0; v < E; v++) x[v] = reduce_any(x[v], m);
+    }
     fwd_rows_body<LOGR, LOGE, false>(x, s, w, q, k1, h, tau);
 #pragma unroll
     for (int v = 0; v < E; v++) s[PAD(tau * E + v)] = reduce4(x[v], q);
