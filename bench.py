@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="catfhe", choices=["catfhe", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the rotation and N=2^14 BFV/BGV side measurements")
     return ap.parse_args()
 
 
@@ -189,6 +191,110 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU leg
 
+def _time(fn, reps):
+    import torch
+    s = torch.cuda.current_stream()
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e-3 / reps
+
+
+def uneven_mix(api, W, R, mm_peak, n_ops=256, lanes=8, reps=5):
+    """256 CKKS operations with N drawn from {2^13 .. 2^16}, levels uniform in
+    2..24, kinds uniform over HMult+relin / HRotate(r in 1..16) / rescale, on
+    one prime chain (q = 1 mod 2^17), tuned NTT schedules, captured once into
+    a CUDA graph over concurrent lanes and replayed."""
+    import numpy as np
+    import torch
+    rng = W.rng_for("uneven-mix")
+    base = W.PRESETS["ckks_n16"]
+    ctxs = {}
+    tuned = {}
+    for log_n in (13, 14, 15, 16):
+        pr = W.Preset(f"mix_n{log_n}", W.CKKS, log_n, base.q_bits, base.p_bits, base.dnum,
+                      log_n_max=16)
+        c = api.Context(pr)
+        k = c.keygen(W.seed_for(f"mix-keys-{log_n}"))
+        gs = [c.galois_elt(r) for r in range(1, 17)]
+        for g in gs:
+            k.gen_galois(g)
+        tuned[log_n] = c.tune_ntt(2 * c.L * 4)
+        ctxs[log_n] = (c, k, gs)
+    ops, keep, work = [], [], 0.0
+    kinds = [api.OP_MUL_RELIN, api.OP_ROTATE, api.OP_RESCALE]
+    seed = W.seed_for("mix-inputs")
+    for i in range(n_ops):
+        log_n = int(rng.choice([13, 14, 15, 16]))
+        level = int(rng.integers(2, 25))
+        kind = kinds[int(rng.integers(0, 3))]
+        c, k, gs = ctxs[log_n]
+        a = c.ct_uniform(seed, 2 * i, level)
+        b = c.ct_uniform(seed, 2 * i + 1, level) if kind == api.OP_MUL_RELIN else None
+        out = c.empty_ct(1, level - 1 if kind == api.OP_RESCALE else level)
+        g = gs[int(rng.integers(0, 16))]
+        ops.append(api.make_op(kind, c, a, out, keys=k, b=b, galois_elt=g))
+        keep.append((a, b, out))
+        if kind == api.OP_MUL_RELIN:
+            w = R.ckks_mul_relin_rescale(c.n, level, c.K, c.alpha).modmuls
+        elif kind == api.OP_ROTATE:
+            w = R.ckks_rotate(c.n, level, c.K, c.alpha).modmuls
+        else:
+            w = (2 + 2 * (level - 1)) * c.n // 2 * log_n + 4 * level * c.n
+        work += w
+    res = {}
+    for nl in (lanes, 1):
+        graph = api.Graph(ops, lanes=nl)
+        t = _time(graph.launch, reps)
+        res[nl] = (t, graph.nodes)
+        graph.close()
+    t, nodes = res[lanes]
+    return {"value": n_ops / t, "unit": "ops/s", "n_ops": n_ops, "lanes": lanes,
+            "graph_nodes": nodes, "ms_per_graph": t * 1e3,
+            "one_lane_ops_per_s": n_ops / res[1][0],
+            "modmul_frac_of_peak": work / t / mm_peak,
+            "ntt_schedules": {f"2^{k}": {"chosen": v[0], "us_per_schedule": v[1]}
+                              for k, v in tuned.items()},
+            "note": "HMult+relin / HRotate / rescale mix over N=2^13..2^16, levels 2..24; "
+                    "frac = sum of per-op modular products / (time x modmul peak)"}
+
+
+def secondary(ctx, keys, a, api, W):
+    """HRotate by r = 1..16 on the batch of 8 (one Galois key each), and
+    HMult+relin on 16 pairs of the N=2^14 BFV and BGV chains."""
+    import torch
+    out = {}
+    gs = [ctx.galois_elt(r) for r in range(1, 17)]
+    for g in gs:
+        keys.gen_galois(g)
+    rot = ctx.empty_ct(*a.shape[:1], a.shape[2])
+
+    def rotate_all():
+        for g in gs:
+            ctx.rotate(keys, a, g, rot)
+    t = _time(rotate_all, 5)
+    out["hrotate_r1_16"] = {"value": a.shape[0] * len(gs) / t, "unit": "HRotate/s",
+                            "note": "8 ciphertexts at level 24, r = 1..16 (16 Galois keys)"}
+    for name in ("bfv_n14", "bgv_n14"):
+        p = W.PRESETS[name]
+        c2 = api.Context(p)
+        k2 = c2.keygen(W.seed_for("bench-keys-" + name))
+        seed = W.seed_for("bench-inputs-" + name)
+        x = torch.cat([c2.ct_uniform(seed, 2 * i, p.L) for i in range(p.batch)])
+        y = torch.cat([c2.ct_uniform(seed, 2 * i + 1, p.L) for i in range(p.batch)])
+        o = c2.empty_ct(p.batch, p.L)
+        t = _time(lambda: c2.mul_relin(k2, x, y, o), 10)
+        out[name] = {"value": p.batch / t, "unit": "HMult+relin/s",
+                     "note": f"N=2^14, 8 x 55-bit q, t=65537, batch {p.batch}"}
+        del c2, k2
+    return out
+
 def run_catfhe(args):
     import numpy as np
     import torch
@@ -313,6 +419,10 @@ def run_catfhe(args):
                "h2d_bytes_per_step": int(ha.numel() * 8 + hb.numel() * 8),
                "d2h_bytes_per_step": int(ho.numel() * 8)}
 
+    side = None
+    if not args.no_secondary:
+        side = secondary(ctx, keys, a, api, W)
+        side["uneven_mix"] = uneven_mix(api, W, R, mm_peak)
     if rank != 0:
         return
     cpu = None
@@ -350,6 +460,7 @@ def run_catfhe(args):
                        "p99": step_ms_sorted[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],
                        "unit": "ms per batched step of 8"},
         "gpu_launches": int(launches),
+        "secondary": side,
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -251,6 +251,59 @@ int catfhe_ntt(catfhe_ctx *ctx, uint64_t *limbs, uint32_t level, uint32_t count,
 int catfhe_measure_int_peak(double *modmul_per_s, double *butterfly_per_s, void *stream);
 uint64_t catfhe_kernel_launches(void);
 
+/* ---- Uneven batches (many independent operations in one submission) ----
+ * Each entry is one operation of any context (ring degree), level and kind;
+ * the entries must not depend on one another.  catfhe_run_batch spreads
+ * them over `lanes` (1..32) concurrent streams forked from `stream`, each
+ * lane with its own slice of `ws` (at least catfhe_batch_workspace_bytes),
+ * assigning operations longest-first by modular-product count, and joins
+ * the lanes back into `stream` (paper Sec. 3.1.6 spreads per-modulus work
+ * over a stream pool; here whole operations are spread).
+ * catfhe_batch_capture runs the batch once, then captures it into a CUDA
+ * graph (buffers and workspace are baked in: replaying it recomputes the
+ * same operations on whatever the buffers then hold); catfhe_graph_launch
+ * replays it on a stream.  The lane streams are shared by all calls on a
+ * device: call from one host thread at a time.  op codes:
+ * CATFHE_OP_MUL_RELIN, CATFHE_OP_MUL_RELIN_RESCALE, CATFHE_OP_ROTATE
+ * (galois_elt used), CATFHE_OP_RESCALE (keys and b unused). */
+typedef struct {
+    int32_t op;
+    uint32_t level;
+    uint32_t count;
+    uint32_t pad;
+    catfhe_ctx *ctx;
+    const catfhe_keys *keys;
+    const uint64_t *a;
+    const uint64_t *b;
+    uint64_t *out;
+    uint64_t galois_elt;
+} catfhe_op;
+
+typedef struct catfhe_graph catfhe_graph;
+
+size_t catfhe_batch_workspace_bytes(const catfhe_op *ops, uint32_t n, uint32_t lanes);
+int catfhe_run_batch(const catfhe_op *ops, uint32_t n, uint32_t lanes, void *ws, size_t ws_bytes,
+                     void *stream);
+int catfhe_batch_capture(const catfhe_op *ops, uint32_t n, uint32_t lanes, void *ws,
+                         size_t ws_bytes, catfhe_graph **out);
+int catfhe_graph_launch(catfhe_graph *graph, void *stream);
+size_t catfhe_graph_nodes(const catfhe_graph *graph);
+void catfhe_graph_destroy(catfhe_graph *graph);
+
+/* ---- NTT schedules (paper Sec. 3.1.3) ----
+ * Each ring degree has a few two-pass schedules (how many of the log N
+ * stages the column pass takes, and how many words each thread holds).
+ * catfhe_tune_ntt times every schedule of ctx's ring degree on `limbs`
+ * limbs (forward + inverse, best of five, synchronises `stream`), keeps the
+ * fastest for all later work of ctx and writes its index to *chosen and each
+ * schedule's time in microseconds to us[] (either may be NULL).
+ * catfhe_ntt_schedule reports the schedule in use, how many exist and its
+ * shape {column log size, column log words/thread, row log size, row log
+ * words/thread}; catfhe_set_ntt_schedule picks one by index. */
+int catfhe_tune_ntt(catfhe_ctx *ctx, uint32_t limbs, void *stream, int32_t *chosen, float *us);
+int catfhe_ntt_schedule(const catfhe_ctx *ctx, int32_t *index, int32_t *count, int32_t shape[4]);
+int catfhe_set_ntt_schedule(catfhe_ctx *ctx, int32_t index);
+
 /* Workspace bytes that `op` needs for `count` ciphertexts at `level`. */
 size_t catfhe_workspace_bytes(const catfhe_ctx *ctx, int op, uint32_t level, uint32_t count);
 

@@ -31,7 +31,9 @@ EXPORTS = [
     "catfhe_ct_import", "catfhe_ct_export", "catfhe_add", "catfhe_mul_relin",
     "catfhe_mul_relin_rescale", "catfhe_rotate", "catfhe_rescale", "catfhe_decrypt",
     "catfhe_ntt", "catfhe_workspace_bytes", "catfhe_measure_int_peak", "catfhe_kernel_launches",
-    "catfhe_rescale_noalloc",
+    "catfhe_rescale_noalloc", "catfhe_batch_workspace_bytes", "catfhe_run_batch",
+    "catfhe_batch_capture", "catfhe_graph_launch", "catfhe_graph_nodes", "catfhe_graph_destroy",
+    "catfhe_tune_ntt", "catfhe_ntt_schedule", "catfhe_set_ntt_schedule",
 ]
 
 
@@ -46,6 +48,14 @@ class Params(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("L", ctypes.c_int32), ("K", ctypes.c_int32),
                 ("nb", ctypes.c_int32), ("alpha", ctypes.c_int32), ("beta", ctypes.c_int32)]
+
+
+class Op(ctypes.Structure):
+    """One entry of an uneven batch (catfhe_op)."""
+    _fields_ = [("op", ctypes.c_int32), ("level", ctypes.c_uint32), ("count", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32), ("ctx", ctypes.c_void_p), ("keys", ctypes.c_void_p),
+                ("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("galois_elt", ctypes.c_uint64)]
 
 
 class CatfheError(RuntimeError):
@@ -95,6 +105,16 @@ def load(path: str = LIB_PATH):
             "catfhe_measure_int_peak": (ctypes.c_int, [vp, vp, vp]),
             "catfhe_kernel_launches": (u64, []),
             "catfhe_rescale_noalloc": (ctypes.c_int, [vp, vp, vp, u32, u32, vp]),
+            "catfhe_batch_workspace_bytes": (sz, [vp, u32, u32]),
+            "catfhe_run_batch": (ctypes.c_int, [vp, u32, u32, vp, sz, vp]),
+            "catfhe_batch_capture": (ctypes.c_int, [vp, u32, u32, vp, sz, ctypes.POINTER(vp)]),
+            "catfhe_graph_launch": (ctypes.c_int, [vp, vp]),
+            "catfhe_graph_nodes": (sz, [vp]),
+            "catfhe_graph_destroy": (None, [vp]),
+            "catfhe_tune_ntt": (ctypes.c_int, [vp, u32, vp, ctypes.POINTER(ctypes.c_int32), vp]),
+            "catfhe_ntt_schedule": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32),
+                                                   ctypes.POINTER(ctypes.c_int32), vp]),
+            "catfhe_set_ntt_schedule": (ctypes.c_int, [vp, ctypes.c_int32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -309,6 +329,25 @@ class Context:
                "catfhe_rescale_noalloc")
         return out
 
+    def tune_ntt(self, limbs: int):
+        """Times every NTT schedule of this ring degree; keeps the fastest."""
+        chosen = ctypes.c_int32()
+        us = (ctypes.c_float * 8)()
+        _check(load().catfhe_tune_ntt(self._h, limbs, _stream(), ctypes.byref(chosen), us),
+               "catfhe_tune_ntt")
+        idx, count, shape = self.ntt_schedule()
+        return chosen.value, [round(us[i], 2) for i in range(count)]
+
+    def ntt_schedule(self):
+        idx, count = ctypes.c_int32(), ctypes.c_int32()
+        shape = (ctypes.c_int32 * 4)()
+        _check(load().catfhe_ntt_schedule(self._h, ctypes.byref(idx), ctypes.byref(count), shape),
+               "catfhe_ntt_schedule")
+        return idx.value, count.value, list(shape)
+
+    def set_ntt_schedule(self, index: int):
+        _check(load().catfhe_set_ntt_schedule(self._h, index), "catfhe_set_ntt_schedule")
+
     def ntt(self, limbs, inverse: bool = False):
         """limbs: int64 tensor [count][level][N], transformed in place."""
         count, level, _ = limbs.shape
@@ -327,6 +366,75 @@ def measure_int_peak() -> tuple[float, float]:
 
 def kernel_launches() -> int:
     return int(load().catfhe_kernel_launches())
+
+
+def make_op(kind: int, ctx: "Context", a, out, keys: "Keys" = None, b=None, galois_elt: int = 0) -> Op:
+    """An entry of an uneven batch: `a`, `b`, `out` are device tensors
+    [count][2][level][N] of ctx's ring degree."""
+    o = Op()
+    o.op = kind
+    o.count, _, o.level, _ = a.shape
+    o.ctx = ctx._h.value
+    o.keys = keys._h.value if keys is not None else None
+    o.a = a.data_ptr()
+    o.b = b.data_ptr() if b is not None else None
+    o.out = out.data_ptr()
+    o.galois_elt = galois_elt
+    return o
+
+
+def _op_array(ops):
+    arr = (Op * len(ops))(*ops)
+    return arr
+
+
+def batch_workspace_bytes(ops, lanes: int) -> int:
+    return int(load().catfhe_batch_workspace_bytes(_op_array(ops), len(ops), lanes))
+
+
+def run_batch(ops, lanes: int, ws=None):
+    """Runs independent operations of any ring degree and level concurrently."""
+    torch = _torch()
+    arr = _op_array(ops)
+    need = load().catfhe_batch_workspace_bytes(arr, len(ops), lanes)
+    if need == 0:
+        raise CatfheError(-1, "catfhe_batch_workspace_bytes")
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    _check(load().catfhe_run_batch(arr, len(ops), lanes, _ptr(ws), ws.numel(), _stream()),
+           "catfhe_run_batch")
+    return ws
+
+
+class Graph:
+    """A captured uneven batch, replayed with launch()."""
+
+    def __init__(self, ops, lanes: int):
+        torch = _torch()
+        self._arr = _op_array(ops)
+        need = load().catfhe_batch_workspace_bytes(self._arr, len(ops), lanes)
+        if need == 0:
+            raise CatfheError(-1, "catfhe_batch_workspace_bytes")
+        self.ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        h = vp()
+        _check(load().catfhe_batch_capture(self._arr, len(ops), lanes, _ptr(self.ws), self.ws.numel(),
+                                           ctypes.byref(h)), "catfhe_batch_capture")
+        self._h = h
+        self.nodes = int(load().catfhe_graph_nodes(h))
+
+    def launch(self):
+        _check(load().catfhe_graph_launch(self._h, _stream()), "catfhe_graph_launch")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().catfhe_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Keys:

@@ -5,13 +5,6 @@
 
 #include "internal.h"
 
-struct catfhe_ctx {
-    catfhe::Context c;
-};
-struct catfhe_keys {
-    catfhe::Keys *k;
-    const catfhe_ctx *owner;
-};
 
 namespace catfhe {
 int ctx_init(Context &c, const catfhe_params &p);

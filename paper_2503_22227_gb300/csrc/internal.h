@@ -128,6 +128,7 @@ struct Context {
     std::map<std::string, uint32_t> plan_sizes;  // words
     Scratch scratch;
     int device = 0;
+    int ntt_sched = 0;  // NTT schedule index for this ring degree (see ntt.cu)
 
     int pq(int i) const { return i; }                // index of q_i
     int pp(int k) const { return L + k; }            // index of p_k
@@ -167,6 +168,10 @@ struct NttEpilogue {
 };
 int launch_ntt_fwd_combine(const Context &c, uint64_t *lift, const LimbMap &map, uint32_t n_limbs,
                            const NttEpilogue &epi, cudaStream_t s);
+
+int ntt_schedule_count(int log_n);
+void ntt_schedule_shape(int log_n, int sched, int shape[4]);
+int tune_ntt(Context &c, uint32_t limbs, cudaStream_t s, int *chosen, float *us_out);
 
 // Exact base conversion (conv.cu): grid over (coefficient, item, plan).
 // grid.z runs plan z over items item = 0..items-1 (grid.y): sources at
@@ -274,3 +279,12 @@ void h_cdt(uint64_t out[19]);
 DevMod h_devmod(uint64_t q, uint64_t n, uint64_t psi);
 
 }  // namespace catfhe
+
+// The opaque handles of the C ABI.
+struct catfhe_ctx {
+    catfhe::Context c;
+};
+struct catfhe_keys {
+    catfhe::Keys *k;
+    const catfhe_ctx *owner;
+};

@@ -380,17 +380,40 @@ static int run_inv(const Context &c, const uint64_t *src, uint64_t *dst, const L
 }
 
 // (column pass log size, its LOGE, row pass log size, its LOGE) per log N
+// Schedules per log N: (column-pass log size, its LOGE, row-pass log size,
+// its LOGE).  Index 0 is the default; catfhe_tune_ntt times them all.
+#define NTT_SCHEDULES(X)                                                        \
+    X(12, 0, 6, 3, 6, 3) X(12, 1, 5, 3, 7, 4) X(12, 2, 7, 4, 5, 3)              \
+    X(13, 0, 7, 4, 6, 3) X(13, 1, 6, 3, 7, 4) X(13, 2, 5, 3, 8, 4)              \
+    X(14, 0, 7, 4, 7, 4) X(14, 1, 6, 3, 8, 4) X(14, 2, 8, 4, 6, 3)              \
+    X(15, 0, 8, 4, 7, 4) X(15, 1, 7, 4, 8, 4)                                   \
+    X(16, 0, 8, 4, 8, 4)
+
+int ntt_schedule_count(int log_n) {
+    switch (log_n) {
+        case 12: case 13: case 14: return 3;
+        case 15: return 2;
+        case 16: return 1;
+        default: return 0;
+    }
+}
+
+void ntt_schedule_shape(int log_n, int sched, int shape[4]) {
+#define SHAPE(LN, S, A, B, C, D) \
+    if (log_n == LN && sched == S) { shape[0] = A; shape[1] = B; shape[2] = C; shape[3] = D; return; }
+    NTT_SCHEDULES(SHAPE)
+#undef SHAPE
+    shape[0] = shape[1] = shape[2] = shape[3] = 0;
+}
+
 static int fwd_dispatch(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
                         uint32_t n_limbs, cudaStream_t s, const NttEpilogue *epi) {
     if (n_limbs == 0) return CATFHE_OK;
-    switch (c.log_n) {
-        case 12: return run_fwd<6, 3, 6, 3>(c, src, dst, map, n_limbs, s, epi);
-        case 13: return run_fwd<7, 4, 6, 3>(c, src, dst, map, n_limbs, s, epi);
-        case 14: return run_fwd<7, 4, 7, 4>(c, src, dst, map, n_limbs, s, epi);
-        case 15: return run_fwd<8, 4, 7, 4>(c, src, dst, map, n_limbs, s, epi);
-        case 16: return run_fwd<8, 4, 8, 4>(c, src, dst, map, n_limbs, s, epi);
-        default: return CATFHE_EINVAL;
-    }
+#define FWD(LN, S, A, B, C, D) \
+    if (c.log_n == LN && c.ntt_sched == S) return run_fwd<A, B, C, D>(c, src, dst, map, n_limbs, s, epi);
+    NTT_SCHEDULES(FWD)
+#undef FWD
+    return CATFHE_EINVAL;
 }
 
 int launch_ntt_fwd(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
@@ -406,14 +429,62 @@ int launch_ntt_fwd_combine(const Context &c, uint64_t *lift, const LimbMap &map,
 int launch_ntt_inv(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
                    uint32_t n_limbs, cudaStream_t s) {
     if (n_limbs == 0) return CATFHE_OK;
-    switch (c.log_n) {
-        case 12: return run_inv<6, 3, 6, 3>(c, src, dst, map, n_limbs, s);
-        case 13: return run_inv<7, 4, 6, 3>(c, src, dst, map, n_limbs, s);
-        case 14: return run_inv<7, 4, 7, 4>(c, src, dst, map, n_limbs, s);
-        case 15: return run_inv<8, 4, 7, 4>(c, src, dst, map, n_limbs, s);
-        case 16: return run_inv<8, 4, 8, 4>(c, src, dst, map, n_limbs, s);
-        default: return CATFHE_EINVAL;
+#define INV(LN, S, A, B, C, D) \
+    if (c.log_n == LN && c.ntt_sched == S) return run_inv<A, B, C, D>(c, src, dst, map, n_limbs, s);
+    NTT_SCHEDULES(INV)
+#undef INV
+    return CATFHE_EINVAL;
+}
+
+// Times every schedule of this ring degree on `limbs` limbs (a forward and an
+// inverse transform each, best of five) and keeps the fastest in the context.
+int tune_ntt(Context &c, uint32_t limbs, cudaStream_t s, int *chosen, float *us_out) {
+    const int count = ntt_schedule_count(c.log_n);
+    if (count == 0 || limbs == 0) return CATFHE_EINVAL;
+    const uint32_t L = uint32_t(c.L);
+    const uint32_t groups = (limbs + L - 1) / L;
+    uint64_t *buf = nullptr;
+    if (cudaMalloc(&buf, size_t(groups) * L * c.n * 8) != cudaSuccess) return CATFHE_ENOMEM;
+    int rc = cudaMemsetAsync(buf, 0, size_t(groups) * L * c.n * 8, s) == cudaSuccess ? CATFHE_OK
+                                                                                     : CATFHE_ECUDA;
+    LimbMap m{};
+    m.period = L;
+    m.src_stride = m.dst_stride = L;
+    for (uint32_t i = 0; i < L; i++) {
+        m.src_off[i] = m.dst_off[i] = uint16_t(i);
+        m.prime[i] = uint8_t(i);
     }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int keep = c.ntt_sched;
+    int best = keep;
+    float best_ms = 1e30f;
+    for (int k = 0; k < count && rc == CATFHE_OK; k++) {
+        c.ntt_sched = k;
+        float t_min = 1e30f;
+        for (int rep = 0; rep < 6 && rc == CATFHE_OK; rep++) {
+            cudaEventRecord(e0, s);
+            rc = launch_ntt_fwd(c, buf, buf, m, groups * L, s);
+            if (!rc) rc = launch_ntt_inv(c, buf, buf, m, groups * L, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = CATFHE_ECUDA;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) t_min = ms < t_min ? ms : t_min;
+        }
+        if (us_out) us_out[k] = t_min * 1e3f;
+        if (t_min < best_ms) {
+            best_ms = t_min;
+            best = k;
+        }
+    }
+    c.ntt_sched = rc == CATFHE_OK ? best : keep;
+    if (chosen) *chosen = c.ntt_sched;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    return rc;
 }
 
 }  // namespace catfhe

@@ -1,0 +1,110 @@
+"""NTT schedules, the schedule tuner, and uneven batches (many operations of
+different ring degrees and levels in one submission, run over concurrent
+lanes and replayed from a captured CUDA graph): every result must equal the
+single-operation results (which the parity tests tie to the oracle)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_22227_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2503_22227_gb300 import api  # noqa: E402
+
+
+@pytest.mark.parametrize("log_n", [12, 13, 14, 15, 16])
+def test_every_ntt_schedule_matches_oracle(log_n):
+    p = W.Preset("sched", W.CKKS, log_n, (50, 58, 61), (60,), 1, log_n_max=16)
+    ctx = api.Context(p)
+    _, count, _ = ctx.ntt_schedule()
+    assert count >= 1
+    rng = np.random.default_rng(100 + log_n)
+    host = W.uniform_residues(rng, ctx.q, (1,), ctx.n)
+    want = [oracle.ntt(host[0, i], log_n, q, oracle.min_psi(q, log_n)) for i, q in enumerate(ctx.q)]
+    for k in range(count):
+        ctx.set_ntt_schedule(k)
+        dev = torch.from_numpy(host.view(np.int64).copy()).cuda()
+        ctx.ntt(dev)
+        got = dev.cpu().numpy().view(np.uint64)
+        for i in range(ctx.L):
+            assert np.array_equal(got[0, i], want[i]), (k, i)
+        ctx.ntt(dev, inverse=True)
+        assert np.array_equal(dev.cpu().numpy().view(np.uint64), host), k
+    chosen, times = ctx.tune_ntt(3 * 8)
+    assert 0 <= chosen < count and len(times) == count and all(t > 0 for t in times)
+    assert ctx.ntt_schedule()[0] == chosen
+
+
+def _ctx(preset, rots):
+    ctx = api.Context(preset)
+    keys = ctx.keygen(W.seed_for("batch-keys-" + preset.name))
+    gs = [ctx.galois_elt(r) for r in rots]
+    for g in gs:
+        keys.gen_galois(g)
+    return ctx, keys, gs
+
+
+def test_uneven_batch_and_graph_equal_single_ops():
+    c12, k12, g12 = _ctx(W.PRESETS["ckks_n12"], (1, 3))
+    c13, k13, g13 = _ctx(W.Preset("ckks_n13", W.CKKS, 13, (45,) * 6, (50, 50), 3, log_n_max=13),
+                         (1, 5))
+    rng = np.random.default_rng(7)
+    jobs = []  # (kind, ctx, keys, level, count, galois)
+    for i in range(14):
+        ctx, keys, gs = (c12, k12, g12) if i % 2 == 0 else (c13, k13, g13)
+        level = int(rng.integers(2, ctx.L + 1))
+        kind = [api.OP_MUL_RELIN, api.OP_MUL_RELIN_RESCALE, api.OP_ROTATE, api.OP_RESCALE][i % 4]
+        count = int(rng.integers(1, 3))
+        jobs.append((kind, ctx, keys, level, count, gs[i % 2]))
+    ops, outs, wants = [], [], []
+    for j, (kind, ctx, keys, level, count, g) in enumerate(jobs):
+        a = torch.cat([ctx.ct_uniform(W.seed_for("batch-in"), 2 * (8 * j + c), level)
+                       for c in range(count)])
+        b = torch.cat([ctx.ct_uniform(W.seed_for("batch-in"), 2 * (8 * j + c) + 1, level)
+                       for c in range(count)])
+        if kind == api.OP_MUL_RELIN:
+            want = ctx.mul_relin(keys, a, b)
+        elif kind == api.OP_MUL_RELIN_RESCALE:
+            want = ctx.mul_relin_rescale(keys, a, b)
+        elif kind == api.OP_ROTATE:
+            want = ctx.rotate(keys, a, g)
+        else:
+            want = ctx.rescale(a)
+        out = torch.zeros_like(want)
+        ops.append(api.make_op(kind, ctx, a, out, keys=keys, b=b, galois_elt=g))
+        outs.append(out)
+        wants.append(want.clone())
+        # keep inputs alive for the graph replays
+        outs[-1]._keep = (a, b)
+    api.run_batch(ops, lanes=4)
+    torch.cuda.synchronize()
+    for j, (o, w) in enumerate(zip(outs, wants)):
+        assert torch.equal(o, w), j
+    graph = api.Graph(ops, lanes=4)
+    assert graph.nodes > len(ops)
+    for o in outs:
+        o.zero_()
+    for _ in range(2):
+        graph.launch()
+    torch.cuda.synchronize()
+    for j, (o, w) in enumerate(zip(outs, wants)):
+        assert torch.equal(o, w), j
+
+
+def test_batch_rejects_bad_entries():
+    ctx, keys, gs = _ctx(W.PRESETS["ckks_n12"], (1,))
+    a = ctx.ct_uniform(W.seed_for("bad"), 0, 1)
+    out = torch.zeros_like(a)
+    with pytest.raises(api.CatfheError) as e:
+        api.run_batch([api.make_op(api.OP_RESCALE, ctx, a, out)], lanes=1)
+    assert e.value.code in (-1, -2)   # rescale at level 1
+    a3 = ctx.ct_uniform(W.seed_for("bad"), 1, 3)
+    out3 = torch.zeros_like(a3)
+    with pytest.raises(api.CatfheError) as e:
+        api.run_batch([api.make_op(api.OP_ROTATE, ctx, a3, out3, keys=keys,
+                                   galois_elt=ctx.galois_elt(9))], lanes=1)
+    assert e.value.code in (-1, -3)   # missing Galois key
