@@ -69,7 +69,13 @@ enum {
     CATFHE_OP_RESCALE = 4,
     CATFHE_OP_DECRYPT = 5,
     CATFHE_OP_EXPORT = 6,
-    CATFHE_OP_NTT = 7
+    CATFHE_OP_NTT = 7,
+    /* element-wise operations (batch entries; no workspace) */
+    CATFHE_OP_ADD = 8,
+    CATFHE_OP_SUB = 9,
+    CATFHE_OP_MUL_INT = 10,
+    CATFHE_OP_ADD_CONST = 11,
+    CATFHE_OP_DROP = 12
 };
 
 /* Forms for catfhe_ct_import / catfhe_ct_export. */
@@ -192,6 +198,28 @@ int catfhe_mul_relin_rescale(catfhe_ctx *ctx, const catfhe_keys *keys, const uin
                              const uint64_t *b, uint64_t *out, uint32_t level,
                              uint32_t count, void *ws, size_t ws_bytes, void *stream);
 
+/* out = a - b (ciphertext subtraction), count ciphertexts at `level`. */
+int catfhe_sub(catfhe_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out,
+               uint32_t level, uint32_t count, void *stream);
+
+/* Multiplication by a plaintext integer constant k (Table 1
+ * "multiply_plain" for a constant plaintext): both polynomials times k mod
+ * q_i, no rescale.  For CKKS multiply by round(c q_{l-1}) and then rescale
+ * to scale by a real c while keeping the scale.  Any scheme. */
+int catfhe_mul_int(catfhe_ctx *ctx, const uint64_t *a, int64_t k, uint64_t *out, uint32_t level,
+                   uint32_t count, void *stream);
+
+/* Addition of the plaintext constant k to every slot (CKKS: k is the
+ * scaled value, round(c * scale); BGV: k mod t): c0 += k, which in NTT form
+ * is the constant polynomial k.  ESCHEME for BFV. */
+int catfhe_add_const(catfhe_ctx *ctx, const uint64_t *a, int64_t k, uint64_t *out,
+                     uint32_t level, uint32_t count, void *stream);
+
+/* Keeps primes q_0 .. q_{new_level-1}: out is u64[count][2][new_level][N]
+ * (CKKS scale and plaintext unchanged); out must not alias a. */
+int catfhe_drop_level(catfhe_ctx *ctx, const uint64_t *a, uint32_t level, uint32_t new_level,
+                      uint64_t *out, uint32_t count, void *stream);
+
 /* Rotation (Table 1 "rotate_vector_one_step", Tables 2-3 rotate rows /
  * columns): out = (sigma_g(a0), 0) + KS(sigma_g(a1)) with the Galois key of
  * g; g = catfhe_galois_elt(steps), or 2N-1 for conjugation / columns. */
@@ -263,20 +291,22 @@ uint64_t catfhe_kernel_launches(void);
  * graph (buffers and workspace are baked in: replaying it recomputes the
  * same operations on whatever the buffers then hold); catfhe_graph_launch
  * replays it on a stream.  The lane streams are shared by all calls on a
- * device: call from one host thread at a time.  op codes:
- * CATFHE_OP_MUL_RELIN, CATFHE_OP_MUL_RELIN_RESCALE, CATFHE_OP_ROTATE
- * (galois_elt used), CATFHE_OP_RESCALE (keys and b unused). */
+ * device: call from one host thread at a time.  op codes and the fields
+ * they use: CATFHE_OP_MUL_RELIN, _MUL_RELIN_RESCALE (keys, a, b, out);
+ * _ROTATE (keys, a, out, arg = Galois element); _RESCALE (a, out);
+ * _ADD, _SUB (a, b, out); _MUL_INT, _ADD_CONST (a, out, arg = the int64
+ * constant as two's complement); _DROP (a, out, level_out). */
 typedef struct {
     int32_t op;
     uint32_t level;
     uint32_t count;
-    uint32_t pad;
+    uint32_t level_out;
     catfhe_ctx *ctx;
     const catfhe_keys *keys;
     const uint64_t *a;
     const uint64_t *b;
     uint64_t *out;
-    uint64_t galois_elt;
+    uint64_t arg;
 } catfhe_op;
 
 typedef struct catfhe_graph catfhe_graph;

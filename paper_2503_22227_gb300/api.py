@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_PKG, "libcatfhe.so")
 
 CKKS, BFV, BGV = 0, 1, 2
 OP_MUL_RELIN, OP_MUL_RELIN_RESCALE, OP_ROTATE, OP_RESCALE, OP_DECRYPT, OP_EXPORT, OP_NTT = range(1, 8)
+OP_ADD, OP_SUB, OP_MUL_INT, OP_ADD_CONST, OP_DROP = range(8, 13)
 FORM_COEFF, FORM_NATIVE = 0, 1
 
 # every symbol include/catfhe.h declares
@@ -34,6 +35,7 @@ EXPORTS = [
     "catfhe_rescale_noalloc", "catfhe_batch_workspace_bytes", "catfhe_run_batch",
     "catfhe_batch_capture", "catfhe_graph_launch", "catfhe_graph_nodes", "catfhe_graph_destroy",
     "catfhe_tune_ntt", "catfhe_ntt_schedule", "catfhe_set_ntt_schedule",
+    "catfhe_sub", "catfhe_mul_int", "catfhe_add_const", "catfhe_drop_level",
 ]
 
 
@@ -53,9 +55,9 @@ class Info(ctypes.Structure):
 class Op(ctypes.Structure):
     """One entry of an uneven batch (catfhe_op)."""
     _fields_ = [("op", ctypes.c_int32), ("level", ctypes.c_uint32), ("count", ctypes.c_uint32),
-                ("pad", ctypes.c_uint32), ("ctx", ctypes.c_void_p), ("keys", ctypes.c_void_p),
+                ("level_out", ctypes.c_uint32), ("ctx", ctypes.c_void_p), ("keys", ctypes.c_void_p),
                 ("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("out", ctypes.c_void_p),
-                ("galois_elt", ctypes.c_uint64)]
+                ("arg", ctypes.c_uint64)]
 
 
 class CatfheError(RuntimeError):
@@ -115,6 +117,10 @@ def load(path: str = LIB_PATH):
             "catfhe_ntt_schedule": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32),
                                                    ctypes.POINTER(ctypes.c_int32), vp]),
             "catfhe_set_ntt_schedule": (ctypes.c_int, [vp, ctypes.c_int32]),
+            "catfhe_sub": (ctypes.c_int, [vp, vp, vp, vp, u32, u32, vp]),
+            "catfhe_mul_int": (ctypes.c_int, [vp, vp, i64, vp, u32, u32, vp]),
+            "catfhe_add_const": (ctypes.c_int, [vp, vp, i64, vp, u32, u32, vp]),
+            "catfhe_drop_level": (ctypes.c_int, [vp, vp, u32, u32, vp, u32, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -288,6 +294,34 @@ class Context:
                "catfhe_add")
         return out
 
+    def sub(self, a, b, out=None):
+        count, _, level, _ = a.shape
+        out = self.empty_ct(count, level) if out is None else out
+        _check(load().catfhe_sub(self._h, _ptr(a), _ptr(b), _ptr(out), level, count, _stream()),
+               "catfhe_sub")
+        return out
+
+    def mul_int(self, a, k: int, out=None):
+        count, _, level, _ = a.shape
+        out = self.empty_ct(count, level) if out is None else out
+        _check(load().catfhe_mul_int(self._h, _ptr(a), k, _ptr(out), level, count, _stream()),
+               "catfhe_mul_int")
+        return out
+
+    def add_const(self, a, k: int, out=None):
+        count, _, level, _ = a.shape
+        out = self.empty_ct(count, level) if out is None else out
+        _check(load().catfhe_add_const(self._h, _ptr(a), k, _ptr(out), level, count, _stream()),
+               "catfhe_add_const")
+        return out
+
+    def drop_level(self, a, new_level: int, out=None):
+        count, _, level, _ = a.shape
+        out = self.empty_ct(count, new_level) if out is None else out
+        _check(load().catfhe_drop_level(self._h, _ptr(a), level, new_level, _ptr(out), count,
+                                        _stream()), "catfhe_drop_level")
+        return out
+
     def mul_relin(self, keys: "Keys", a, b, out=None):
         count, _, level, _ = a.shape
         out = self.empty_ct(count, level) if out is None else out
@@ -368,18 +402,21 @@ def kernel_launches() -> int:
     return int(load().catfhe_kernel_launches())
 
 
-def make_op(kind: int, ctx: "Context", a, out, keys: "Keys" = None, b=None, galois_elt: int = 0) -> Op:
+def make_op(kind: int, ctx: "Context", a, out, keys: "Keys" = None, b=None, galois_elt: int = 0,
+            const: int = 0) -> Op:
     """An entry of an uneven batch: `a`, `b`, `out` are device tensors
-    [count][2][level][N] of ctx's ring degree."""
+    [count][2][level][N] of ctx's ring degree.  galois_elt for rotations,
+    const (int64) for MUL_INT / ADD_CONST; DROP takes the level of `out`."""
     o = Op()
     o.op = kind
     o.count, _, o.level, _ = a.shape
+    o.level_out = out.shape[2]
     o.ctx = ctx._h.value
     o.keys = keys._h.value if keys is not None else None
     o.a = a.data_ptr()
     o.b = b.data_ptr() if b is not None else None
     o.out = out.data_ptr()
-    o.galois_elt = galois_elt
+    o.arg = galois_elt if kind == OP_ROTATE else (const & 0xFFFFFFFFFFFFFFFF)
     return o
 
 

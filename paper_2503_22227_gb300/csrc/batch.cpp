@@ -27,6 +27,16 @@ int op_rotate(Context &c, const Keys &keys, const uint64_t *a, uint64_t g, uint6
               uint32_t level, uint32_t count, void *ws, size_t ws_bytes_in, cudaStream_t s);
 int op_rescale(Context &c, const uint64_t *a, uint64_t *out, uint32_t level, uint32_t count,
                void *ws, size_t ws_bytes_in, cudaStream_t s);
+int op_add(Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t level,
+           uint32_t count, cudaStream_t s);
+int op_sub(Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t level,
+           uint32_t count, cudaStream_t s);
+int op_mul_int(Context &c, const uint64_t *a, int64_t k, uint64_t *out, uint32_t level,
+               uint32_t count, cudaStream_t s);
+int op_add_const(Context &c, const uint64_t *a, int64_t k, uint64_t *out, uint32_t level,
+                 uint32_t count, cudaStream_t s);
+int op_drop_level(Context &c, const uint64_t *a, uint32_t level, uint32_t new_level,
+                  uint64_t *out, uint32_t count, cudaStream_t s);
 
 namespace {
 
@@ -62,11 +72,9 @@ int lane_pool(LanePool **out) {
     return CATFHE_OK;
 }
 
-int ws_code(int op) {
-    return op == CATFHE_OP_MUL_RELIN_RESCALE ? CATFHE_OP_MUL_RELIN_RESCALE
-           : op == CATFHE_OP_ROTATE          ? CATFHE_OP_ROTATE
-           : op == CATFHE_OP_RESCALE         ? CATFHE_OP_RESCALE
-                                             : CATFHE_OP_MUL_RELIN;
+bool needs_ws(int op) {
+    return op == CATFHE_OP_MUL_RELIN || op == CATFHE_OP_MUL_RELIN_RESCALE ||
+           op == CATFHE_OP_ROTATE || op == CATFHE_OP_RESCALE;
 }
 
 int check_op(const catfhe_op &o) {
@@ -84,13 +92,23 @@ int check_op(const catfhe_op &o) {
             return o.keys->k->ksk.count(0) ? CATFHE_OK : CATFHE_ENOKEY;
         case CATFHE_OP_ROTATE: {
             if (!o.keys || o.keys->owner != o.ctx) return CATFHE_EINVAL;
-            const uint64_t g = o.galois_elt % (2 * c.n);
+            const uint64_t g = o.arg % (2 * c.n);
             if (!(g & 1)) return CATFHE_EINVAL;
             return o.keys->k->ksk.count(g) ? CATFHE_OK : CATFHE_ENOKEY;
         }
         case CATFHE_OP_RESCALE:
             if (c.scheme == CATFHE_BFV) return CATFHE_ESCHEME;
             return o.level >= 2 ? CATFHE_OK : CATFHE_ELEVEL;
+        case CATFHE_OP_ADD:
+        case CATFHE_OP_SUB:
+            return o.b ? CATFHE_OK : CATFHE_EINVAL;
+        case CATFHE_OP_MUL_INT:
+            return CATFHE_OK;
+        case CATFHE_OP_ADD_CONST:
+            return c.scheme == CATFHE_BFV ? CATFHE_ESCHEME : CATFHE_OK;
+        case CATFHE_OP_DROP:
+            return (o.level_out >= 1 && o.level_out <= o.level && o.a != o.out) ? CATFHE_OK
+                                                                            : CATFHE_ELEVEL;
         default:
             return CATFHE_EINVAL;
     }
@@ -101,6 +119,7 @@ int check_op(const catfhe_op &o) {
 double op_cost(const catfhe_op &o) {
     const Context &c = o.ctx->c;
     const double n = double(c.n), lg = double(c.log_n), l = double(o.level), K = double(c.K);
+    if (!needs_ws(o.op)) return o.count * 2 * l * n;
     if (o.op == CATFHE_OP_RESCALE) return o.count * ((2 + 2 * (l - 1)) * n / 2 * lg + 4 * l * n);
     const double M = l + K;
     double ntt = l, prod = 4 * l;
@@ -140,7 +159,7 @@ int plan_batch(const catfhe_op *ops, uint32_t n, uint32_t lanes, Plan &p) {
         load[l] += cost[i];
         p.lane_ops[l].push_back(i);
         const catfhe_op &o = ops[i];
-        const size_t w = ws_bytes(o.ctx->c, ws_code(o.op), o.level, o.count);
+        const size_t w = needs_ws(o.op) ? ws_bytes(o.ctx->c, o.op, o.level, o.count) : 0;
         p.lane_ws[l] = std::max(p.lane_ws[l], (w + 255) & ~size_t(255));
     }
     // within a lane, run in submission order
@@ -158,9 +177,19 @@ int run_one(const catfhe_op &o, void *ws, size_t ws_bytes_in, cudaStream_t s) {
         case CATFHE_OP_MUL_RELIN_RESCALE:
             return op_mul_relin(c, *o.keys->k, o.a, o.b, o.out, o.level, o.count, true, ws, ws_bytes_in, s);
         case CATFHE_OP_ROTATE:
-            return op_rotate(c, *o.keys->k, o.a, o.galois_elt, o.out, o.level, o.count, ws, ws_bytes_in, s);
+            return op_rotate(c, *o.keys->k, o.a, o.arg, o.out, o.level, o.count, ws, ws_bytes_in, s);
         case CATFHE_OP_RESCALE:
             return op_rescale(c, o.a, o.out, o.level, o.count, ws, ws_bytes_in, s);
+        case CATFHE_OP_ADD:
+            return op_add(c, o.a, o.b, o.out, o.level, o.count, s);
+        case CATFHE_OP_SUB:
+            return op_sub(c, o.a, o.b, o.out, o.level, o.count, s);
+        case CATFHE_OP_MUL_INT:
+            return op_mul_int(c, o.a, int64_t(o.arg), o.out, o.level, o.count, s);
+        case CATFHE_OP_ADD_CONST:
+            return op_add_const(c, o.a, int64_t(o.arg), o.out, o.level, o.count, s);
+        case CATFHE_OP_DROP:
+            return op_drop_level(c, o.a, o.level, o.level_out, o.out, o.count, s);
         default:
             return CATFHE_EINVAL;
     }

@@ -21,6 +21,14 @@ int op_add(Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out, uint
            uint32_t count, cudaStream_t s);
 int op_ntt(Context &c, uint64_t *limbs, uint32_t level, uint32_t count, int inverse,
            cudaStream_t s);
+int op_sub(Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t level,
+           uint32_t count, cudaStream_t s);
+int op_mul_int(Context &c, const uint64_t *a, int64_t k, uint64_t *out, uint32_t level,
+               uint32_t count, cudaStream_t s);
+int op_add_const(Context &c, const uint64_t *a, int64_t k, uint64_t *out, uint32_t level,
+                 uint32_t count, cudaStream_t s);
+int op_drop_level(Context &c, const uint64_t *a, uint32_t level, uint32_t new_level,
+                  uint64_t *out, uint32_t count, cudaStream_t s);
 int op_keygen(Context &c, const uint8_t seed[32], Keys **out);
 int op_gen_galois(Context &c, Keys &k, uint64_t g);
 void keys_free(Keys *k);
@@ -175,6 +183,30 @@ int catfhe_add(catfhe_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *
                uint32_t level, uint32_t count, void *stream) {
     if (!ctx || !a || !b || !out) return CATFHE_EINVAL;
     return op_add(ctx->c, a, b, out, level, count, S(stream));
+}
+
+int catfhe_sub(catfhe_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out,
+               uint32_t level, uint32_t count, void *stream) {
+    if (!ctx || !a || !b || !out) return CATFHE_EINVAL;
+    return op_sub(ctx->c, a, b, out, level, count, S(stream));
+}
+
+int catfhe_mul_int(catfhe_ctx *ctx, const uint64_t *a, int64_t k, uint64_t *out, uint32_t level,
+                   uint32_t count, void *stream) {
+    if (!ctx || !a || !out) return CATFHE_EINVAL;
+    return op_mul_int(ctx->c, a, k, out, level, count, S(stream));
+}
+
+int catfhe_add_const(catfhe_ctx *ctx, const uint64_t *a, int64_t k, uint64_t *out,
+                     uint32_t level, uint32_t count, void *stream) {
+    if (!ctx || !a || !out) return CATFHE_EINVAL;
+    return op_add_const(ctx->c, a, k, out, level, count, S(stream));
+}
+
+int catfhe_drop_level(catfhe_ctx *ctx, const uint64_t *a, uint32_t level, uint32_t new_level,
+                      uint64_t *out, uint32_t count, void *stream) {
+    if (!ctx || !a || !out || a == out) return CATFHE_EINVAL;
+    return op_drop_level(ctx->c, a, level, new_level, out, count, S(stream));
 }
 
 int catfhe_mul_relin(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,

@@ -220,6 +220,56 @@ int launch_add(const Context &c, const uint64_t *a, const uint64_t *b, uint64_t 
     return ok();
 }
 
+// out = a - b over a map (same layout for a, b, out).
+__global__ void __launch_bounds__(256)
+k_sub(const uint64_t *__restrict__ a, const uint64_t *__restrict__ b, uint64_t *out,
+      const LimbMap map, const DevMod *__restrict__ mods, uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const uint32_t limb = blockIdx.y, g = limb / map.period, r = limb % map.period;
+    const size_t o = (size_t(g) * map.src_stride + map.src_off[r]) * n + x;
+    out[o] = sub_mod(a[o], b[o], mods[map.prime[r]].q);
+}
+
+int launch_sub(const Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out,
+               const LimbMap &map, uint32_t n_limbs, cudaStream_t s) {
+    k_sub<<<coeff_grid(c.n, n_limbs), 256, 0, s>>>(a, b, out, map, c.d_mods, c.log_n);
+    return ok();
+}
+
+// out = a * k_r (a constant per map entry, Shoup pair), or a + k_r on the
+// entries with add_mask set (adding a constant polynomial in NTT form).
+struct ConstArgs {
+    uint64_t k[kMapMax], k_s[kMapMax];
+    uint8_t add[kMapMax];
+};
+
+__global__ void __launch_bounds__(256)
+k_const_op(const uint64_t *__restrict__ a, uint64_t *out, const LimbMap map, const ConstArgs C,
+           const DevMod *__restrict__ mods, uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const uint32_t limb = blockIdx.y, g = limb / map.period, r = limb % map.period;
+    const size_t o = (size_t(g) * map.src_stride + map.src_off[r]) * n + x;
+    const uint64_t q = mods[map.prime[r]].q;
+    out[o] = C.add[r] ? add_mod(a[o], C.k[r], q) : shoup(a[o], C.k[r], C.k_s[r], q);
+}
+
+int launch_const_op(const Context &c, const uint64_t *a, uint64_t *out, const LimbMap &map,
+                    uint32_t n_limbs, const uint64_t *k, const uint64_t *k_s, const uint8_t *add,
+                    cudaStream_t s) {
+    ConstArgs C{};
+    for (uint32_t r = 0; r < map.period; r++) {
+        C.k[r] = k[r];
+        C.k_s[r] = k_s[r];
+        C.add[r] = add[r];
+    }
+    k_const_op<<<coeff_grid(c.n, n_limbs), 256, 0, s>>>(a, out, map, C, c.d_mods, c.log_n);
+    return ok();
+}
+
 __global__ void __launch_bounds__(256)
 k_copy(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, const LimbMap map,
        uint32_t log_n) {

@@ -234,6 +234,12 @@ int launch_add(const Context &c, const uint64_t *a, const uint64_t *b, uint64_t 
                const LimbMap &map, uint32_t n_limbs, cudaStream_t s);
 int launch_copy_limbs(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
                       uint32_t n_limbs, cudaStream_t s);
+int launch_sub(const Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out,
+               const LimbMap &map, uint32_t n_limbs, cudaStream_t s);
+// per map entry r: out = a * k[r] (Shoup pair k_s[r]), or a + k[r] where add[r]
+int launch_const_op(const Context &c, const uint64_t *a, uint64_t *out, const LimbMap &map,
+                    uint32_t n_limbs, const uint64_t *k, const uint64_t *k_s, const uint8_t *add,
+                    cudaStream_t s);
 
 // Sampling (sample.cu)
 enum SampleKind { kUniform = 0, kTernary = 1, kGaussian = 2 };

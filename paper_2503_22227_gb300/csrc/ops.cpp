@@ -664,6 +664,88 @@ int op_add(Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out, uint
     return launch_add(c, a, b, out, m, 2 * level * count, s);
 }
 
+static LimbMap map_ct(uint32_t level) {
+    LimbMap m{};
+    m.period = 2 * level;
+    m.src_stride = m.dst_stride = 2 * level;
+    for (uint32_t i = 0; i < 2 * level; i++) {
+        m.src_off[i] = m.dst_off[i] = uint16_t(i);
+        m.prime[i] = uint8_t(i % level);
+    }
+    return m;
+}
+
+int op_sub(Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t level,
+           uint32_t count, cudaStream_t s) {
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    if (count == 0) return CATFHE_OK;
+    return launch_sub(c, a, b, out, map_ct(level), 2 * level * count, s);
+}
+
+static uint64_t reduce_signed(int64_t v, uint64_t q) {
+    const uint64_t mag = v < 0 ? uint64_t(0) - uint64_t(v) : uint64_t(v);
+    const uint64_t r = mag % q;
+    return (v < 0 && r) ? q - r : r;
+}
+
+// Both polynomials times the integer k (any scheme; no rescale).
+int op_mul_int(Context &c, const uint64_t *a, int64_t k, uint64_t *out, uint32_t level,
+               uint32_t count, cudaStream_t s) {
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    if (count == 0) return CATFHE_OK;
+    const LimbMap m = map_ct(level);
+    std::vector<uint64_t> kv(2 * level), ks(2 * level);
+    std::vector<uint8_t> add(2 * level, 0);
+    for (uint32_t i = 0; i < 2 * level; i++) {
+        const uint64_t q = c.mod(int(i % level));
+        kv[i] = reduce_signed(k, q);
+        ks[i] = h_shoup(kv[i], q);
+    }
+    return launch_const_op(c, a, out, m, 2 * level * count, kv.data(), ks.data(), add.data(), s);
+}
+
+// Adds the plaintext constant k to every slot: c0 += k (the constant
+// polynomial k, which is k at every evaluation point in NTT form) for CKKS
+// and BGV; for BFV (coefficient form) c0 += Delta k at coefficient 0 is not
+// an element-wise map, so BFV is not supported here.
+int op_add_const(Context &c, const uint64_t *a, int64_t k, uint64_t *out, uint32_t level,
+                 uint32_t count, cudaStream_t s) {
+    if (c.scheme == CATFHE_BFV) return CATFHE_ESCHEME;
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    if (count == 0) return CATFHE_OK;
+    const LimbMap m = map_ct(level);
+    std::vector<uint64_t> kv(2 * level, 1), ks(2 * level);
+    std::vector<uint8_t> add(2 * level, 0);
+    for (uint32_t i = 0; i < 2 * level; i++) {
+        const uint64_t q = c.mod(int(i % level));
+        if (i < level) {
+            kv[i] = reduce_signed(k, q);
+            add[i] = 1;
+        }
+        ks[i] = h_shoup(kv[i], q);
+    }
+    return launch_const_op(c, a, out, m, 2 * level * count, kv.data(), ks.data(), add.data(), s);
+}
+
+// Keeps the first new_level limbs of each polynomial (dropping primes keeps
+// the message and, in CKKS, the scale).
+int op_drop_level(Context &c, const uint64_t *a, uint32_t level, uint32_t new_level,
+                  uint64_t *out, uint32_t count, cudaStream_t s) {
+    if (level < 1 || int(level) > c.L || new_level < 1 || new_level > level) return CATFHE_ELEVEL;
+    if (count == 0) return CATFHE_OK;
+    LimbMap m{};
+    m.period = 2 * new_level;
+    m.src_stride = 2 * level;
+    m.dst_stride = 2 * new_level;
+    for (uint32_t p = 0; p < 2; p++)
+        for (uint32_t i = 0; i < new_level; i++) {
+            m.src_off[p * new_level + i] = uint16_t(p * level + i);
+            m.dst_off[p * new_level + i] = uint16_t(p * new_level + i);
+            m.prime[p * new_level + i] = uint8_t(i);
+        }
+    return launch_copy_limbs(c, a, out, m, 2 * new_level * count, s);
+}
+
 int op_ntt(Context &c, uint64_t *limbs, uint32_t level, uint32_t count, int inverse,
            cudaStream_t s) {
     if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
