@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the rotation and N=2^14 BFV/BGV side measurements")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the private-query serving sweep")
     return ap.parse_args()
 
 
@@ -295,6 +297,47 @@ def secondary(ctx, keys, a, api, W):
         del c2, k2
     return out
 
+def serving_sweep(W, fracs=(0.1, 0.5, 0.8, 1.5), lanes=8, max_active=64):
+    """The private-query workload (1000 x 4 encrypted table, N=2^16, L=24,
+    K=8): the saturation rate from a burst of 64 requests, then Poisson
+    arrivals at fractions of it; p50/p99 latency (arrival to result in host
+    memory) and throughput per rate."""
+    import torch
+
+    from paper_2503_22227_gb300 import serving as S
+    table = S.Table(W.PRESETS["ckks_n16_k8"], bound_pairs=8)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(min(max_active * table.need, 0.8 * free))
+    eng = S.GpuEngine(table, lanes=lanes, keep_results=False)
+    S.serve(S.make_requests(table, 8, 0.0, "serve-warm"), eng, budget, max_active)
+    torch.cuda.synchronize()
+    burst = S.serve(S.make_requests(table, 64, 0.0, "serve-burst"), eng, budget, max_active)
+    mu = burst.throughput
+    points = []
+    for f in fracs:
+        rate = f * mu
+        count = int(min(192, max(32, rate * 3.0)))
+        st = S.serve(S.make_requests(table, count, rate, f"serve-{f}"), eng, budget, max_active)
+        points.append({"offered_per_s": rate, "requests": count, "throughput_per_s": st.throughput,
+                       **st.latency, "mean_active": st.mean_active, "max_active": st.max_active,
+                       "joined_running_batch": st.admitted_while_busy, "ticks": st.ticks})
+    counts = table.circuit.counts()
+    head = points[1] if len(points) > 1 else points[0]
+    out = {"unit": "queries/s", "saturation_per_s": mu,
+           "burst64": {"throughput_per_s": mu, **burst.latency, "ticks": burst.ticks},
+           "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
+           "at_offered_per_s": head["offered_per_s"], "sweep": points,
+           "request": {"rows": S.ROWS, "columns": S.COLS, "stages": len(table.circuit.stages()),
+                       "ops": {k: v for k, v in counts.items() if k != "input"},
+                       "reserved_bytes": table.need},
+           "budget_bytes": budget, "max_active": max_active, "lanes": lanes,
+           "note": "latency from Poisson arrival to the encrypted answer in pinned host memory; "
+                   "p50/p99 at the second sweep point (0.5 x saturation)"}
+    del eng, table
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_catfhe(args):
     import numpy as np
     import torch
@@ -423,6 +466,9 @@ def run_catfhe(args):
     if not args.no_secondary:
         side = secondary(ctx, keys, a, api, W)
         side["uneven_mix"] = uneven_mix(api, W, R, mm_peak)
+    serving = None
+    if not args.no_serving:
+        serving = serving_sweep(W)
     if rank != 0:
         return
     cpu = None
@@ -460,6 +506,8 @@ def run_catfhe(args):
                        "p99": step_ms_sorted[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],
                        "unit": "ms per batched step of 8"},
         "gpu_launches": int(launches),
+        "p99_ms": serving["p99_ms"] if serving else None,
+        "serving": serving,
         "secondary": side,
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
     }

@@ -80,6 +80,9 @@ enum {
 
 /* Forms for catfhe_ct_import / catfhe_ct_export. */
 enum { CATFHE_FORM_COEFF = 0, CATFHE_FORM_NATIVE = 1 };
+/* OR-ed into the form of catfhe_ct_import / catfhe_ct_export: return
+ * without synchronising; the copy completes in the order of `stream`. */
+enum { CATFHE_FORM_ASYNC = 0x100 };
 
 /*
  * Parameter set (paper Sec. 2.2: q = prod q_i of word-sized coprime
@@ -170,7 +173,11 @@ int catfhe_ct_uniform(catfhe_ctx *ctx, const uint8_t seed[32], uint32_t index,
  * FORM_COEFF: host data in coefficient form (converted to / from the at-
  * rest form on the device).  FORM_NATIVE: host data in the at-rest form
  * (plain copies).  export needs workspace only for FORM_COEFF; it
- * synchronises `stream`.  import synchronises on the host copy. */
+ * synchronises `stream`.  import synchronises on the host copy.  With
+ * CATFHE_FORM_ASYNC neither synchronises: the host buffer must then stay
+ * allocated and unchanged (import) or unread (export) until the work
+ * enqueued on `stream` so far has completed; page-locked host memory lets
+ * the copy overlap with other work. */
 int catfhe_ct_import(catfhe_ctx *ctx, const uint64_t *host, uint32_t level, uint32_t count,
                      int form, uint64_t *ct, void *stream);
 int catfhe_ct_export(catfhe_ctx *ctx, const uint64_t *ct, uint32_t level, uint32_t count,

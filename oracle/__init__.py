@@ -104,6 +104,10 @@ def lib():
                 "oc_decrypt": (None, [ctypes.c_void_p, ctypes.c_void_p, u64p, ctypes.c_int,
                                       ctypes.c_uint64, i64p]),
                 "oc_add": (None, [ctypes.c_void_p, u64p, u64p, u64p, ctypes.c_int]),
+                "oc_sub": (None, [ctypes.c_void_p, u64p, u64p, u64p, ctypes.c_int]),
+                "oc_mul_int": (None, [ctypes.c_void_p, u64p, ctypes.c_int64, u64p, ctypes.c_int]),
+                "oc_add_const": (None, [ctypes.c_void_p, u64p, ctypes.c_int64, u64p, ctypes.c_int]),
+                "oc_drop": (None, [ctypes.c_void_p, u64p, ctypes.c_int, ctypes.c_int, u64p]),
                 "oc_keyswitch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, u64p, ctypes.c_int,
                                                 ctypes.c_uint64, u64p]),
                 "oc_rescale": (None, [ctypes.c_void_p, u64p, u64p, ctypes.c_int]),
@@ -308,6 +312,31 @@ class Context:
         b = np.ascontiguousarray(b, dtype=np.uint64)
         out = np.zeros_like(a)
         lib().oc_add(self._h, _u64(a), _u64(b), _u64(out), a.shape[1])
+        return out
+
+    def sub(self, a, b):
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        b = np.ascontiguousarray(b, dtype=np.uint64)
+        out = np.zeros_like(a)
+        lib().oc_sub(self._h, _u64(a), _u64(b), _u64(out), a.shape[1])
+        return out
+
+    def mul_int(self, a, k: int):
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        out = np.zeros_like(a)
+        lib().oc_mul_int(self._h, _u64(a), int(k), _u64(out), a.shape[1])
+        return out
+
+    def add_const(self, a, k: int):
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        out = np.zeros_like(a)
+        lib().oc_add_const(self._h, _u64(a), int(k), _u64(out), a.shape[1])
+        return out
+
+    def drop(self, a, new_level: int):
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        out = np.zeros((2, new_level, self.n), dtype=np.uint64)
+        lib().oc_drop(self._h, _u64(a), a.shape[1], new_level, _u64(out))
         return out
 
     def tensor(self, a, b):

@@ -468,6 +468,52 @@ void oc_add(const void *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out
             }
 }
 
+/* Ciphertext subtraction (Table 1 "sub"): out = a - b limb by limb. */
+void oc_sub(const void *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out, int level) {
+    const oc_ctx *c = ctx;
+    uint64_t n = c->n;
+    for (int p = 0; p < 2; p++)
+        for (int i = 0; i < level; i++)
+            for (uint64_t j = 0; j < n; j++) {
+                size_t o = ((size_t)p * (size_t)level + (size_t)i) * n + j;
+                out[o] = oc_submod(a[o], b[o], c->q[i]);
+            }
+}
+
+/* Multiplication by the integer k (a constant plaintext, Table 1
+ * "multiply_plain"): both polynomials times k mod q_i. */
+void oc_mul_int(const void *ctx, const uint64_t *a, int64_t k, uint64_t *out, int level) {
+    const oc_ctx *c = ctx;
+    uint64_t n = c->n;
+    for (int p = 0; p < 2; p++)
+        for (int i = 0; i < level; i++) {
+            uint64_t kq = oc_reduce_i64(k, c->q[i]);
+            for (uint64_t j = 0; j < n; j++) {
+                size_t o = ((size_t)p * (size_t)level + (size_t)i) * n + j;
+                out[o] = oc_mulmod(a[o], kq, c->q[i]);
+            }
+        }
+}
+
+/* Adds the constant polynomial k to the plaintext: coefficient 0 of c0
+ * plus k mod q_i (coefficient form); everything else copied. */
+void oc_add_const(const void *ctx, const uint64_t *a, int64_t k, uint64_t *out, int level) {
+    const oc_ctx *c = ctx;
+    uint64_t n = c->n;
+    memcpy(out, a, sizeof(uint64_t) * 2 * (size_t)level * n);
+    for (int i = 0; i < level; i++)
+        out[(size_t)i * n] = oc_addmod(a[(size_t)i * n], oc_reduce_i64(k, c->q[i]), c->q[i]);
+}
+
+/* Level drop: keeps the limbs of q_0 .. q_{new_level-1} of each polynomial. */
+void oc_drop(const void *ctx, const uint64_t *a, int level, int new_level, uint64_t *out) {
+    const oc_ctx *c = ctx;
+    uint64_t n = c->n;
+    for (int p = 0; p < 2; p++)
+        memcpy(out + (size_t)p * (size_t)new_level * n, a + (size_t)p * (size_t)level * n,
+               sizeof(uint64_t) * (size_t)new_level * n);
+}
+
 /* Key switch of one polynomial cin (over Q_l) with key `id`:
  * (k0, k1) with k0 + k1 s = cin s' + small (CKKS, BFV) or + t small (BGV). */
 int oc_keyswitch(const void *ctx, const void *keys, const uint64_t *cin, int level,

@@ -23,6 +23,7 @@ CKKS, BFV, BGV = 0, 1, 2
 OP_MUL_RELIN, OP_MUL_RELIN_RESCALE, OP_ROTATE, OP_RESCALE, OP_DECRYPT, OP_EXPORT, OP_NTT = range(1, 8)
 OP_ADD, OP_SUB, OP_MUL_INT, OP_ADD_CONST, OP_DROP = range(8, 13)
 FORM_COEFF, FORM_NATIVE = 0, 1
+FORM_ASYNC = 0x100      # OR-ed into a form: import / export without synchronising
 
 # every symbol include/catfhe.h declares
 EXPORTS = [

@@ -188,19 +188,32 @@ class Circuit:
         return rec(c)
 
     # ------------------------------------------------------------ analysis
+    def live(self) -> set:
+        """Nodes the outputs depend on (the others are never run)."""
+        seen, todo = set(), list(self.outputs.values())
+        while todo:
+            i = todo.pop()
+            if i not in seen:
+                seen.add(i)
+                todo.extend(self.nodes[i].args)
+        return seen
+
     def stages(self) -> list[list[int]]:
         out: dict[int, list[int]] = {}
+        live = self.live()
         for nd in self.nodes:
-            if nd.kind != "input":
+            if nd.kind != "input" and nd.id in live:
                 out.setdefault(nd.stage, []).append(nd.id)
         return [out[k] for k in sorted(out)]
 
     def peak_bytes(self) -> int:
         """Largest total size of live intermediate ciphertexts over the stages."""
         last_use = {}
+        alive = self.live()
         for nd in self.nodes:
-            for a in nd.args:
-                last_use[a] = max(last_use.get(a, 0), nd.stage)
+            if nd.id in alive:
+                for a in nd.args:
+                    last_use[a] = max(last_use.get(a, 0), nd.stage)
         for o in self.outputs.values():
             last_use[o] = 1 << 30
         live, peak = {}, 0
@@ -215,9 +228,12 @@ class Circuit:
         return peak
 
     def counts(self) -> dict:
+        """Operations run per request, by kind (live nodes only)."""
         c: dict[str, int] = {}
+        live = self.live()
         for nd in self.nodes:
-            c[nd.kind] = c.get(nd.kind, 0) + 1
+            if nd.id in live:
+                c[nd.kind] = c.get(nd.kind, 0) + 1
         return c
 
     # ------------------------------------------------------------ float reference
@@ -251,6 +267,49 @@ class Circuit:
         return {k: v[i] for k, i in self.outputs.items()}
 
 
+_OP_KIND = {"sub": api.OP_SUB, "add": api.OP_ADD, "mul": api.OP_MUL_RELIN_RESCALE,
+            "mul_int": api.OP_MUL_INT, "rescale": api.OP_RESCALE, "add_const": api.OP_ADD_CONST,
+            "drop": api.OP_DROP, "rotate": api.OP_ROTATE}
+
+
+@dataclass
+class Schedule:
+    """Per-stage entries (node id, op kind, argument ids, level, integer
+    argument) and the node ids whose buffers may be released after each stage."""
+    stages: list
+    release: list
+
+
+def schedule(circuit: Circuit) -> Schedule:
+    cached = getattr(circuit, "_schedule", None)
+    if cached is not None and cached[0] == len(circuit.nodes):
+        return cached[1]
+    groups = circuit.stages()
+    live = circuit.live()
+    last_use: dict[int, int] = {}
+    for nd in circuit.nodes:
+        if nd.id in live:
+            for a in nd.args:
+                last_use[a] = max(last_use.get(a, 0), nd.stage)
+    keep = set(circuit.outputs.values()) | set(circuit.inputs.values())
+    by_stage: dict[int, list] = {}
+    for i, s in last_use.items():
+        if i not in keep:
+            by_stage.setdefault(s, []).append(i)
+    stages, release = [], []
+    for g in groups:
+        entries = []
+        for i in g:
+            nd = circuit.nodes[i]
+            arg = nd.galois if nd.kind == "rotate" else nd.const
+            entries.append((i, _OP_KIND[nd.kind], nd.args, nd.level, arg))
+        stages.append(entries)
+        release.append(by_stage.get(circuit.nodes[g[0]].stage, []))
+    sch = Schedule(stages, release)
+    circuit._schedule = (len(circuit.nodes), sch)
+    return sch
+
+
 class Runner:
     """One request's instance of a circuit: device buffers per node, the
     batch entries of the current stage, and buffer release after last use."""
@@ -261,43 +320,39 @@ class Runner:
         self.buf: dict[int, object] = {}
         for name, i in circuit.inputs.items():
             self.buf[i] = inputs[name]
-        self.stages = circuit.stages()
+        self.sch = schedule(circuit)
         self.pos = 0
-        self.last_use = {}
-        for nd in circuit.nodes:
-            for a in nd.args:
-                self.last_use[a] = max(self.last_use.get(a, 0), nd.stage)
-        self.keep = set(circuit.outputs.values()) | set(circuit.inputs.values())
 
     @property
     def done(self) -> bool:
-        return self.pos >= len(self.stages)
+        return self.pos >= len(self.sch.stages)
+
+    @property
+    def remaining(self) -> int:
+        return len(self.sch.stages) - self.pos
 
     def stage_ops(self) -> list:
         ops = []
-        for i in self.stages[self.pos]:
-            nd = self.c.nodes[i]
-            a = self.buf[nd.args[0]]
-            out = self.ctx.empty_ct(a.shape[0], nd.level)
+        for i, kind, args, level, arg in self.sch.stages[self.pos]:
+            a = self.buf[args[0]]
+            out = self.ctx.empty_ct(a.shape[0], level)
             self.buf[i] = out
-            kind = {"sub": api.OP_SUB, "add": api.OP_ADD, "mul": api.OP_MUL_RELIN_RESCALE,
-                    "mul_int": api.OP_MUL_INT, "rescale": api.OP_RESCALE,
-                    "add_const": api.OP_ADD_CONST, "drop": api.OP_DROP,
-                    "rotate": api.OP_ROTATE}[nd.kind]
-            b = self.buf[nd.args[1]] if len(nd.args) > 1 else None
+            b = self.buf[args[1]] if len(args) > 1 else None
             ops.append(api.make_op(kind, self.ctx, a, out, keys=self.keys, b=b,
-                                   galois_elt=nd.galois, const=nd.const))
+                                   galois_elt=arg if kind == api.OP_ROTATE else 0,
+                                   const=0 if kind == api.OP_ROTATE else arg))
         return ops
 
     def advance(self) -> None:
-        s = self.c.nodes[self.stages[self.pos][0]].stage
-        for i in list(self.buf):
-            if i not in self.keep and self.last_use.get(i, 1 << 30) <= s:
-                del self.buf[i]
+        for i in self.sch.release[self.pos]:
+            self.buf.pop(i, None)
         self.pos += 1
 
     def result(self, name: str):
         return self.buf[self.c.outputs[name]]
+
+    def release(self) -> None:
+        self.buf.clear()
 
 
 def pdq_circuit(ctx, delta: float, coeffs, kappa: float = 1.0, sum_slots: int = 1024,

@@ -39,9 +39,9 @@ int op_encrypt(Context &c, const Keys &k, const int64_t *msg, const uint8_t seed
 int op_ct_uniform(Context &c, const uint8_t seed[32], uint32_t index, uint32_t level, uint64_t *ct,
                   cudaStream_t s);
 int op_import(Context &c, const uint64_t *host, uint32_t level, uint32_t count, int form,
-              uint64_t *ct, cudaStream_t s);
+              bool sync, uint64_t *ct, cudaStream_t s);
 int op_export(Context &c, const uint64_t *ct, uint32_t level, uint32_t count, int form,
-              uint64_t *host, void *ws, size_t ws_bytes_in, cudaStream_t s);
+              bool sync, uint64_t *host, void *ws, size_t ws_bytes_in, cudaStream_t s);
 int op_decrypt(Context &c, const Keys &k, const uint64_t *ct, uint32_t level, uint64_t factor,
                int64_t *msg, void *ws, size_t ws_bytes_in, cudaStream_t s);
 int measure_int_peak(double *modmul_per_s, double *bfly_per_s, cudaStream_t s);
@@ -165,18 +165,27 @@ int catfhe_ct_uniform(catfhe_ctx *ctx, const uint8_t seed[32], uint32_t index, u
     return op_ct_uniform(ctx->c, seed, index, level, ct, S(stream));
 }
 
+static bool split_form(int form, int *base, bool *sync) {
+    if (form & ~(0xff | CATFHE_FORM_ASYNC)) return false;
+    *base = form & 0xff;
+    *sync = !(form & CATFHE_FORM_ASYNC);
+    return *base == CATFHE_FORM_COEFF || *base == CATFHE_FORM_NATIVE;
+}
+
 int catfhe_ct_import(catfhe_ctx *ctx, const uint64_t *host, uint32_t level, uint32_t count,
                      int form, uint64_t *ct, void *stream) {
-    if (!ctx || !host || !ct || (form != CATFHE_FORM_COEFF && form != CATFHE_FORM_NATIVE))
-        return CATFHE_EINVAL;
-    return op_import(ctx->c, host, level, count, form, ct, S(stream));
+    int base;
+    bool sync;
+    if (!ctx || !host || !ct || !split_form(form, &base, &sync)) return CATFHE_EINVAL;
+    return op_import(ctx->c, host, level, count, base, sync, ct, S(stream));
 }
 
 int catfhe_ct_export(catfhe_ctx *ctx, const uint64_t *ct, uint32_t level, uint32_t count,
                      int form, uint64_t *host, void *ws, size_t ws_bytes, void *stream) {
-    if (!ctx || !host || !ct || (form != CATFHE_FORM_COEFF && form != CATFHE_FORM_NATIVE))
-        return CATFHE_EINVAL;
-    return op_export(ctx->c, ct, level, count, form, host, ws, ws_bytes, S(stream));
+    int base;
+    bool sync;
+    if (!ctx || !host || !ct || !split_form(form, &base, &sync)) return CATFHE_EINVAL;
+    return op_export(ctx->c, ct, level, count, base, sync, host, ws, ws_bytes, S(stream));
 }
 
 int catfhe_add(catfhe_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out,

@@ -1044,7 +1044,7 @@ int op_ct_uniform(Context &c, const uint8_t seed[32], uint32_t index, uint32_t l
 }
 
 int op_import(Context &c, const uint64_t *host, uint32_t level, uint32_t count, int form,
-              uint64_t *ct, cudaStream_t s) {
+              bool sync, uint64_t *ct, cudaStream_t s) {
     if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
     const size_t bytes = size_t(count) * 2 * level * c.n * 8;
     if (cudaMemcpyAsync(ct, host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return CATFHE_ECUDA;
@@ -1052,11 +1052,12 @@ int op_import(Context &c, const uint64_t *host, uint32_t level, uint32_t count, 
         LimbMap m = map_identity(level);
         TRY(launch_ntt_fwd(c, ct, ct, m, 2 * level * count, s));
     }
+    if (!sync) return CATFHE_OK;
     return cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
 }
 
 int op_export(Context &c, const uint64_t *ct, uint32_t level, uint32_t count, int form,
-              uint64_t *host, void *ws, size_t ws_bytes_in, cudaStream_t s) {
+              bool sync, uint64_t *host, void *ws, size_t ws_bytes_in, cudaStream_t s) {
     if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
     const size_t bytes = size_t(count) * 2 * level * c.n * 8;
     const uint64_t *src = ct;
@@ -1070,6 +1071,7 @@ int op_export(Context &c, const uint64_t *ct, uint32_t level, uint32_t count, in
         src = tmp;
     }
     if (cudaMemcpyAsync(host, src, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CATFHE_ECUDA;
+    if (!sync) return CATFHE_OK;
     return cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
 }
 

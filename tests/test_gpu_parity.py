@@ -211,6 +211,62 @@ def test_ckks_accuracy(ckks12):
     assert np.max(np.abs(z - np.roll(za, -1))) < 2.0 ** -20
 
 
+@pytest.mark.parametrize("preset", [W.PRESETS["ckks_n12"], SMALL_BGV, SMALL_BFV],
+                         ids=lambda p: p.name)
+def test_elementwise_ops_match_oracle(preset):
+    """sub, integer multiply, constant add (not BFV), level drop: direct
+    calls and the same entries through an uneven batch, at a full and a
+    lower level, with positive, negative and zero constants."""
+    pr = Pair(preset)
+    L = preset.L
+    for level in (L, max(1, L - 1)):
+        a, b = _uniform_pair(pr, level, 2, f"ew-{preset.name}-{level}")
+        da, db = pr.g.import_ct(a), pr.g.import_ct(b)
+        got = pr.g.export_ct(pr.g.sub(da, db))
+        for c in range(2):
+            assert np.array_equal(got[c], pr.o.sub(a[c], b[c]))
+        for k in (0, 3, -(2 ** 40) - 7, 2 ** 62 + 11):
+            got = pr.g.export_ct(pr.g.mul_int(da, k))
+            for c in range(2):
+                assert np.array_equal(got[c], pr.o.mul_int(a[c], k)), k
+            if preset.scheme != W.BFV:
+                got = pr.g.export_ct(pr.g.add_const(da, k))
+                for c in range(2):
+                    assert np.array_equal(got[c], pr.o.add_const(a[c], k)), k
+        for nl in range(1, level + 1):
+            got = pr.g.export_ct(pr.g.drop_level(da, nl))
+            for c in range(2):
+                assert np.array_equal(got[c], pr.o.drop(a[c], nl)), nl
+        # the same through one batch
+        entries, outs, wants = [], [], []
+        kinds = [(api.OP_SUB, 0, level), (api.OP_MUL_INT, -12345, level),
+                 (api.OP_DROP, 0, max(1, level - 1))]
+        if preset.scheme != W.BFV:
+            kinds.append((api.OP_ADD_CONST, 987654321, level))
+        for kind, k, lo in kinds:
+            out = pr.g.empty_ct(2, lo)
+            entries.append(api.make_op(kind, pr.g, da, out, b=db if kind == api.OP_SUB else None,
+                                       const=k))
+            outs.append(out)
+            if kind == api.OP_SUB:
+                wants.append([pr.o.sub(a[c], b[c]) for c in range(2)])
+            elif kind == api.OP_MUL_INT:
+                wants.append([pr.o.mul_int(a[c], k) for c in range(2)])
+            elif kind == api.OP_DROP:
+                wants.append([pr.o.drop(a[c], lo) for c in range(2)])
+            else:
+                wants.append([pr.o.add_const(a[c], k) for c in range(2)])
+        api.run_batch(entries, lanes=2)
+        for out, want in zip(outs, wants):
+            got = pr.g.export_ct(out)
+            for c in range(2):
+                assert np.array_equal(got[c], want[c])
+    if preset.scheme == W.BFV:
+        with pytest.raises(api.CatfheError) as e:
+            pr.g.add_const(pr.g.import_ct(_uniform_pair(pr, L, 1, "ew-bfv")[0]), 1)
+        assert e.value.code == -6     # ESCHEME
+
+
 # ---------------------------------------------------------------- hot path, BGV / BFV
 
 @pytest.mark.parametrize("preset", [SMALL_BGV, SMALL_BFV], ids=lambda p: p.name)
@@ -308,3 +364,21 @@ def test_error_codes(ckks12):
     with pytest.raises(api.CatfheError) as e:
         bfv.rescale(x)
     assert e.value.code == -6  # ESCHEME
+
+
+def test_async_import_export_round_trip(ckks12):
+    pr = ckks12
+    a, _ = _uniform_pair(pr, 3, 2, "async-io")
+    host = torch.from_numpy(a.view(np.int64).copy()).pin_memory()
+    dev = pr.g.import_ct(host, api.FORM_COEFF | api.FORM_ASYNC)
+    back = torch.empty_like(host).pin_memory()
+    pr.g.export_into(dev, back, api.FORM_NATIVE | api.FORM_ASYNC)
+    native = torch.empty_like(host).pin_memory()
+    pr.g.export_into(dev, native, api.FORM_NATIVE)
+    torch.cuda.synchronize()
+    assert torch.equal(back, native)
+    dev2 = pr.g.import_ct(back, api.FORM_NATIVE | api.FORM_ASYNC)
+    assert np.array_equal(pr.g.export_ct(dev2, api.FORM_COEFF), a)
+    with pytest.raises(api.CatfheError) as e:
+        pr.g.import_ct(host, api.FORM_NATIVE | 0x200)
+    assert e.value.code == -1

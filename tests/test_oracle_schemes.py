@@ -232,3 +232,45 @@ def test_ckks_keyswitch_output_matches_definition_small():
             for x in range(n):
                 y = round(__import__("fractions").Fraction(acc[poly][x] % QP, P))
                 assert [int(got[poly, i, x]) for i in range(level)] == [y % q for q in ctx.q[:level]]
+
+
+def test_elementwise_ops_by_decryption(bgv_small, ckks_n12):
+    """sub / integer multiply / constant add / level drop, pinned by what
+    decryption must give (exact for BGV mod t; exact integers for CKKS,
+    whose decryption is the centred plaintext polynomial)."""
+    ctx, keys = bgv_small
+    n, t = ctx.n, ctx.t
+    rng = np.random.default_rng(21)
+    a, b = W.int_messages(rng, n, t), W.int_messages(rng, n, t)
+    ca = ctx.encrypt(keys, a, W.seed_for("ew-a"))
+    cb = ctx.encrypt(keys, b, W.seed_for("ew-b"))
+    assert np.array_equal(ctx.decrypt(keys, ctx.sub(ca, cb)), (a - b) % t)
+    assert np.array_equal(ctx.add(ctx.sub(ca, cb), cb), ca)
+    for k in (0, 1, 7, -3, t - 1):
+        assert np.array_equal(ctx.decrypt(keys, ctx.mul_int(ca, k)), (a * k) % t)
+    # BGV in coefficient form: the constant k lands on plaintext coefficient 0
+    want = a.copy()
+    want[0] = (want[0] + 5) % t
+    assert np.array_equal(ctx.decrypt(keys, ctx.add_const(ca, 5)), want)
+    d = ctx.drop(ca, ctx.L - 1)
+    assert d.shape == (2, ctx.L - 1, n)
+    assert np.array_equal(d, ca[:, : ctx.L - 1])
+    # dropping a prime is a modulus switch without the division: the
+    # plaintext survives when the noise is far below the smaller modulus
+    assert np.array_equal(ctx.decrypt(keys, d), a)
+
+    ctx, keys = ckks_n12
+    n = ctx.n
+    rng = np.random.default_rng(22)
+    ma = rng.integers(-2 ** 30, 2 ** 30, n)
+    mb = rng.integers(-2 ** 30, 2 ** 30, n)
+    ca = ctx.encrypt(keys, ma, W.seed_for("ew-ckks-a"))
+    cb = ctx.encrypt(keys, mb, W.seed_for("ew-ckks-b"))
+    da, db = ctx.decrypt(keys, ca), ctx.decrypt(keys, cb)
+    assert np.max(np.abs(da - ma)) < 2 ** 12            # fresh-encryption noise
+    assert np.array_equal(ctx.decrypt(keys, ctx.sub(ca, cb)), da - db)
+    assert np.array_equal(ctx.decrypt(keys, ctx.mul_int(ca, -1234)), da * -1234)
+    want = da.copy()
+    want[0] += -(2 ** 35)
+    assert np.array_equal(ctx.decrypt(keys, ctx.add_const(ca, -(2 ** 35))), want)
+    assert np.array_equal(ctx.decrypt(keys, ctx.drop(ca, 1)), da)
