@@ -52,30 +52,18 @@ def parse():
 # ---------------------------------------------------------------- distributed helpers
 
 def dist_init(n_gpus):
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        backend = "nccl"
-        dist.init_process_group(backend)
-    return rank, world, local
+    from paper_2503_22227_gb300 import replicas
+    return replicas.init_from_env()
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_2503_22227_gb300 import replicas
+    replicas.barrier(world)
 
 
 def max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2503_22227_gb300 import replicas
+    return replicas.max_over_ranks(x, world, "cuda")
 
 
 # ---------------------------------------------------------------- clocks
@@ -309,9 +297,22 @@ def serving_sweep(W, fracs=(0.1, 0.5, 0.8, 1.5), lanes=8, max_active=64):
     free, _ = torch.cuda.mem_get_info()
     budget = int(min(max_active * table.need, 0.8 * free))
     eng = S.GpuEngine(table, lanes=lanes, keep_results=False)
-    S.serve(S.make_requests(table, 8, 0.0, "serve-warm"), eng, budget, max_active)
+    # warm-up: a full burst, so the allocator holds the memory of 64 requests
+    S.serve(S.make_requests(table, max_active, 0.0, "serve-warm"), eng, budget, max_active)
     torch.cuda.synchronize()
-    burst = S.serve(S.make_requests(table, 64, 0.0, "serve-burst"), eng, budget, max_active)
+    # one request alone, and a burst of 64, with host and device time split
+    prof = {}
+    for name, count in (("alone", 1), ("burst64", max_active)):
+        eng.profile = True
+        eng.reset_profile()
+        st = S.serve(S.make_requests(table, count, 0.0, "serve-prof"), eng, budget, max_active)
+        dev = eng.device_busy_s()
+        prof[name] = {"wall_ms": st.wall_s * 1e3, "device_busy_ms": dev * 1e3,
+                      "host_stage_ms": eng.host_stage_s * 1e3,
+                      "host_submit_ms": eng.host_submit_s * 1e3, "ticks": eng.n_ticks,
+                      "ops": eng.n_ops}
+        eng.profile = False
+    burst = S.serve(S.make_requests(table, max_active, 0.0, "serve-burst"), eng, budget, max_active)
     mu = burst.throughput
     points = []
     for f in fracs:
@@ -325,6 +326,7 @@ def serving_sweep(W, fracs=(0.1, 0.5, 0.8, 1.5), lanes=8, max_active=64):
     head = points[1] if len(points) > 1 else points[0]
     out = {"unit": "queries/s", "saturation_per_s": mu,
            "burst64": {"throughput_per_s": mu, **burst.latency, "ticks": burst.ticks},
+           "profile": prof,
            "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
            "at_offered_per_s": head["offered_per_s"], "sweep": points,
            "request": {"rows": S.ROWS, "columns": S.COLS, "stages": len(table.circuit.stages()),
@@ -382,7 +384,8 @@ def run_catfhe(args):
     clk = clocks.stop() if clocks else None
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
     total_s = max_over_ranks(ev[0].elapsed_time(ev[K]) * 1e-3, world)
-    value = world * BATCH * K / total_s
+    from paper_2503_22227_gb300 import replicas
+    value = replicas.throughput(BATCH * K, world, total_s)
 
     # ---- single-ciphertext launches for the same work
     def single_step():

@@ -444,6 +444,25 @@ def run_batch(ops, lanes: int, ws=None):
     return ws
 
 
+class Batch:
+    """An uneven batch marshalled once: the entry array serves both the
+    workspace query and the submission."""
+
+    def __init__(self, ops):
+        self.n = len(ops)
+        self.arr = _op_array(ops)
+
+    def workspace_bytes(self, lanes: int) -> int:
+        need = int(load().catfhe_batch_workspace_bytes(self.arr, self.n, lanes))
+        if need == 0:
+            raise CatfheError(-1, "catfhe_batch_workspace_bytes")
+        return need
+
+    def run(self, lanes: int, ws) -> None:
+        _check(load().catfhe_run_batch(self.arr, self.n, lanes, _ptr(ws), ws.numel(), _stream()),
+               "catfhe_run_batch")
+
+
 class Graph:
     """A captured uneven batch, replayed with launch()."""
 

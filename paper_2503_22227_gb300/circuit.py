@@ -344,6 +344,8 @@ class Runner:
         return ops
 
     def advance(self) -> None:
+        """Drops the buffers last read by the current stage; call it only
+        after that stage has been enqueued."""
         for i in self.sch.release[self.pos]:
             self.buf.pop(i, None)
         self.pos += 1

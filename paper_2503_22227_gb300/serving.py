@@ -121,8 +121,9 @@ def serve(requests: list, engine, budget_bytes: int, max_active: int = 64, depth
     engine protocol:
       need(req) -> bytes          device memory the request reserves
       start(req)                  upload its inputs, set req.state
-      stage(reqs) -> list         build the next stage's entries of each, advance them
-      submit(entries)             enqueue them as one batch (non-blocking)
+      stage(reqs) -> list         build the next stage's entries of each
+      submit(entries)             enqueue them as one batch (non-blocking) and move
+                                  each request past that stage
       is_done(req) -> bool        no stage left
       finish(req)                 enqueue the copy of the result to the host, drop buffers
       mark() -> token             a marker after everything enqueued so far
@@ -272,7 +273,8 @@ class GpuEngine:
     stream-ordered), so no tick waits for the host; result buffers come from
     a pool and return to it when the request retires."""
 
-    def __init__(self, table: Table, lanes: int = 8, keep_results: bool = True):
+    def __init__(self, table: Table, lanes: int = 8, keep_results: bool = True,
+                 profile: bool = False):
         from . import circuit
         self.t = table
         self.api, self.torch = table.api, table.torch
@@ -280,7 +282,21 @@ class GpuEngine:
         self.lanes = lanes
         self.keep = keep_results
         self.ws = None
+        self.staged: list = []
         self.free_hosts: list = []
+        self.profile = profile
+        self.reset_profile()
+
+    def reset_profile(self) -> None:
+        self.host_stage_s = self.host_submit_s = 0.0
+        self.n_ops = self.n_ticks = 0
+        self.tick_events: list = []
+
+    def device_busy_s(self) -> float:
+        """Sum over profiled ticks of the device time from the start to the
+        end of each batch (synchronises)."""
+        self.torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in self.tick_events) * 1e-3
 
     def need(self, req) -> int:
         return self.t.need
@@ -295,19 +311,38 @@ class GpuEngine:
                                              "y": self.t.columns[req.col_b], "lo": lo, "hi": hi})
 
     def stage(self, reqs) -> list:
+        t0 = time.perf_counter()
         entries = []
         for r in reqs:
             entries.extend(r.state.stage_ops())
-            r.state.advance()
+        self.staged = list(reqs)
+        self.host_stage_s += time.perf_counter() - t0
         return entries
 
     def submit(self, entries):
         api, torch = self.api, self.torch
-        need = api.batch_workspace_bytes(entries, self.lanes)
+        t0 = time.perf_counter()
+        batch = api.Batch(entries)
+        need = batch.workspace_bytes(self.lanes)
         if self.ws is None or self.ws.numel() < need:
             self.ws = None
             self.ws = torch.empty(max(need, 1 << 20), dtype=torch.uint8, device="cuda")
-        api.run_batch(entries, self.lanes, self.ws)
+        if self.profile:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+        batch.run(self.lanes, self.ws)
+        if self.profile:
+            e1.record()
+            self.tick_events.append((e0, e1))
+        self.n_ops += len(entries)
+        self.n_ticks += 1
+        # Buffers whose last reader is in this batch go back to the allocator
+        # only now: released before the submission, their memory could be
+        # handed to another request's output within the same batch.
+        for r in self.staged:
+            r.state.advance()
+        self.staged = []
+        self.host_submit_s += time.perf_counter() - t0
 
     def is_done(self, req) -> bool:
         return req.state.done

@@ -240,3 +240,113 @@ def test_idle_gaps_do_not_count_as_latency():
     assert reqs[1].admitted >= 10.0
     assert all(r.latency < 0.05 for r in reqs)
     assert st.latency["max_ms"] < 50
+
+
+# ----------------------------------------------------------------------------
+# The GPU engine's buffer lifetimes, with a fake allocator that recycles
+# addresses as soon as a buffer is dropped (as a caching allocator may).
+
+class _Alloc:
+    def __init__(self):
+        self.free, self.next, self.live = [], 1 << 20, set()
+
+    def take(self):
+        addr = self.free.pop() if self.free else self.next
+        if addr == self.next:
+            self.next += 1 << 20
+        self.live.add(addr)
+        return addr
+
+    def give(self, addr):
+        self.live.discard(addr)
+        self.free.append(addr)
+
+
+class _Buf:
+    def __init__(self, alloc, shape):
+        import weakref
+        self.shape = shape
+        self._p = alloc.take()
+        weakref.finalize(self, alloc.give, self._p)
+
+    def data_ptr(self):
+        return self._p
+
+
+def _fake_table(alloc, batches):
+    import ctypes
+    from paper_2503_22227_gb300 import api as real_api
+
+    ctx = _ctx()
+    ctx._h = ctypes.c_void_p(1)
+    ctx.empty_ct = lambda count, level: _Buf(alloc, (count, 2, level, ctx.n))
+    ctx.import_ct = lambda host, form: _Buf(alloc, (1, 2, ctx.L, ctx.n))
+    ctx.export_into = lambda ct, host, form: host
+    keys = types.SimpleNamespace(_h=ctypes.c_void_p(2))
+
+    def run_batch(entries, lanes, ws):
+        ins = {e.a for e in entries} | {e.b for e in entries if e.b}
+        outs = [e.out for e in entries]
+        assert len(set(outs)) == len(outs), "two outputs share memory"
+        assert not (ins & set(outs)), "an output overwrites an input of the same batch"
+        assert ins <= alloc.live and set(outs) <= alloc.live, "a batch reads released memory"
+        batches.append(len(entries))
+
+    class _Batch:
+        def __init__(self, entries):
+            self.entries = entries
+
+        def workspace_bytes(self, lanes):
+            return 1
+
+        def run(self, lanes, ws):
+            run_batch(self.entries, lanes, ws)
+
+    fake_api = types.SimpleNamespace(
+        FORM_NATIVE=real_api.FORM_NATIVE, FORM_ASYNC=real_api.FORM_ASYNC, Batch=_Batch)
+
+    class _Event:
+        def record(self):
+            pass
+
+        def query(self):
+            return True
+
+        def synchronize(self):
+            pass
+
+    class _Host:
+        def clone(self):
+            return self
+
+    class _Ws:
+        def numel(self):
+            return 1 << 30
+
+    fake_torch = types.SimpleNamespace(
+        uint8=None, int64=None,
+        empty=lambda *a, **k: _Host() if k.get("pin_memory") else _Ws(),
+        cuda=types.SimpleNamespace(Event=_Event))
+    t = S.Table.__new__(S.Table)
+    t.api, t.torch, t.ctx, t.keys = fake_api, fake_torch, ctx, keys
+    t.circuit = C.pdq_circuit(ctx, 2.0 ** 50, S.sign_coefficients())
+    t.columns = [_Buf(alloc, (1, 2, ctx.L, ctx.n)) for _ in range(S.COLS)]
+    t.uploads = [(None, None)] * 4
+    t.need = t.circuit.peak_bytes()
+    return t
+
+
+def test_gpu_engine_never_recycles_a_buffer_inside_its_batch():
+    alloc, batches = _Alloc(), []
+    table = _fake_table(alloc, batches)
+    eng = S.GpuEngine(table, lanes=4)
+    reqs = [S.Request(id=i, arrival=0.002 * i, col_a=i % 4, col_b=(i + 1) % 4, bounds=i % 4)
+            for i in range(12)]
+    clock = iter(np.arange(0, 1e3, 1e-4))
+    st = S.serve(reqs, eng, budget_bytes=5 * table.need, max_active=5,
+                 clock=lambda: next(clock), idle=lambda s: None)
+    assert st.served == 12 and max(batches) > 45
+    assert all(r.result is not None for r in reqs)
+    del reqs, eng
+    # every intermediate went back: only the table columns stay allocated
+    assert len(alloc.live) == S.COLS
