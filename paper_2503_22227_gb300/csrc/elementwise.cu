@@ -61,9 +61,70 @@ int launch_tensor(const Context &c, const TensorArgs &a, uint32_t count, cudaStr
 // The batch item is the fastest-varying block index, so the CTAs of all
 // ciphertexts that read one block of the evaluation key are dispatched back
 // to back: the key crosses HBM once per batch and is served from L2 after.
-template <int BMAX>
+//
+// Every load of a thread is issued before its first multiply (BETA is the
+// exact digit count for the common small cases), so a warp keeps 2 + 3 BETA
+// 16-byte loads in flight instead of stalling on each digit in turn.
+template <int BETA>
+__device__ __forceinline__ void ip_body(const IpArgs &A, const DevMod &m, uint32_t item,
+                                        uint32_t i, size_t n, size_t x, uint32_t beta) {
+    const uint32_t KL = A.L + A.K;
+    const bool own_here = A.own != nullptr && i < A.level;
+    const uint32_t own_digit = own_here ? i / A.alpha : 0xffffffffu;
+    const uint64_t *ext = A.ext + item * A.ext_item;
+    const bool fold = i < A.level && A.pfac[i] != 0;
+    ulonglong2 d0 = make_ulonglong2(0, 0), d1 = make_ulonglong2(0, 0);
+    if (fold && A.add0) d0 = ld2(A.add0 + item * A.add_item + size_t(i) * n + x);
+    if (fold && A.add1) d1 = ld2(A.add1 + item * A.add_item + size_t(i) * n + x);
+    ulonglong2 c[BETA], kb[BETA], ka[BETA];
+#pragma unroll
+    for (int j = 0; j < BETA; j++) {
+        if (uint32_t(j) < beta) {
+            c[j] = (uint32_t(j) == own_digit) ? ld2(A.own + item * A.own_item + size_t(i) * n + x)
+                                              : ld2(ext + (size_t(j) * A.M + i) * n + x);
+            kb[j] = ld2(A.key + ((size_t(j) * 2 + 0) * KL + A.key_limb[i]) * n + x);
+            ka[j] = ld2(A.key + ((size_t(j) * 2 + 1) * KL + A.key_limb[i]) * n + x);
+        }
+    }
+    // keys (and P) are in Montgomery form: one reduction per sum
+    U128 a0{0, 0}, a1{0, 0}, b0{0, 0}, b1{0, 0};
+    if (fold) {
+        const uint64_t pf = A.pfac[i];
+        mac(a0, d0.x, pf);
+        mac(a1, d0.y, pf);
+        mac(b0, d1.x, pf);
+        mac(b1, d1.y, pf);
+    }
+#pragma unroll
+    for (int j = 0; j < BETA; j++) {
+        if (uint32_t(j) < beta) {
+            mac(a0, c[j].x, kb[j].x);
+            mac(a1, c[j].y, kb[j].y);
+            mac(b0, c[j].x, ka[j].x);
+            mac(b1, c[j].y, ka[j].y);
+        }
+    }
+    uint64_t *y = A.y + item * A.y_item;
+    st2(y + size_t(i) * n + x, csub(redc(a0, m.q, m.qinv), m.q), csub(redc(a1, m.q, m.qinv), m.q));
+    st2(y + (size_t(A.M) + i) * n + x, csub(redc(b0, m.q, m.qinv), m.q),
+        csub(redc(b1, m.q, m.qinv), m.q));
+}
+
+template <int BETA>
 __global__ void __launch_bounds__(256)
 k_ip(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const uint32_t item = blockIdx.x, i = blockIdx.z;
+    const size_t x = 2 * (size_t(blockIdx.y) * blockDim.x + threadIdx.x);
+    if (x >= n) return;
+    const DevMod m = mods[A.prime[i]];
+    ip_body<BETA>(A, m, item, i, n, x, A.beta);
+}
+
+// Many digits (beta > 8): digit by digit, loads interleaved with products,
+// so registers stay bounded.
+__global__ void __launch_bounds__(256)
+k_ip_stream(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
     const size_t n = size_t(1) << log_n;
     const uint32_t item = blockIdx.x, i = blockIdx.z;
     const size_t x = 2 * (size_t(blockIdx.y) * blockDim.x + threadIdx.x);
@@ -73,7 +134,6 @@ k_ip(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
     const bool own_here = A.own != nullptr && i < A.level;
     const uint32_t own_digit = own_here ? i / A.alpha : 0xffffffffu;
     const uint64_t *ext = A.ext + item * A.ext_item;
-    // keys (and P) are in Montgomery form: one reduction per sum
     U128 a0{0, 0}, a1{0, 0}, b0{0, 0}, b1{0, 0};
     if (i < A.level && A.pfac[i] != 0) {
         if (A.add0) {
@@ -87,19 +147,15 @@ k_ip(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
             mac(b1, d.y, A.pfac[i]);
         }
     }
-#pragma unroll
-    for (int j = 0; j < BMAX; j++) {
-        if (uint32_t(j) < A.beta) {
-            const ulonglong2 c = (uint32_t(j) == own_digit)
-                                     ? ld2(A.own + item * A.own_item + size_t(i) * n + x)
-                                     : ld2(ext + (size_t(j) * A.M + i) * n + x);
-            const ulonglong2 kb = ld2(A.key + ((size_t(j) * 2 + 0) * KL + A.key_limb[i]) * n + x);
-            const ulonglong2 ka = ld2(A.key + ((size_t(j) * 2 + 1) * KL + A.key_limb[i]) * n + x);
-            mac(a0, c.x, kb.x);
-            mac(a1, c.y, kb.y);
-            mac(b0, c.x, ka.x);
-            mac(b1, c.y, ka.y);
-        }
+    for (uint32_t j = 0; j < A.beta; j++) {
+        const ulonglong2 c = (j == own_digit) ? ld2(A.own + item * A.own_item + size_t(i) * n + x)
+                                              : ld2(ext + (size_t(j) * A.M + i) * n + x);
+        const ulonglong2 kb = ld2(A.key + ((size_t(j) * 2 + 0) * KL + A.key_limb[i]) * n + x);
+        const ulonglong2 ka = ld2(A.key + ((size_t(j) * 2 + 1) * KL + A.key_limb[i]) * n + x);
+        mac(a0, c.x, kb.x);
+        mac(a1, c.y, kb.y);
+        mac(b0, c.x, ka.x);
+        mac(b1, c.y, ka.y);
     }
     uint64_t *y = A.y + item * A.y_item;
     st2(y + size_t(i) * n + x, csub(redc(a0, m.q, m.qinv), m.q), csub(redc(a1, m.q, m.qinv), m.q));
@@ -109,14 +165,17 @@ k_ip(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
 
 int launch_ip(const Context &c, const IpArgs &a, uint32_t count, cudaStream_t s) {
     const dim3 g(count, unsigned((c.n / 2 + 255) / 256), a.M);
-    if (a.beta <= 4)
-        k_ip<4><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n);
-    else if (a.beta <= 8)
-        k_ip<8><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n);
-    else if (a.beta <= 16)
-        k_ip<16><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n);
-    else
-        k_ip<32><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n);
+    switch (a.beta) {
+        case 1: k_ip<1><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n); break;
+        case 2: k_ip<2><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n); break;
+        case 3: k_ip<3><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n); break;
+        case 4: k_ip<4><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n); break;
+        default:
+            if (a.beta <= 8)
+                k_ip<8><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n);
+            else
+                k_ip_stream<<<g, 256, 0, s>>>(a, c.d_mods, c.log_n);
+    }
     return ok();
 }
 

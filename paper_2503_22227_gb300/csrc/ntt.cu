@@ -74,6 +74,14 @@ __device__ __forceinline__ uint64_t reduce_any(uint64_t x, const DevMod &m) {
 
 constexpr uint64_t kWideBound = uint64_t(1) << 58;
 
+// (tau E + v) >> sh for 0 <= v < E = 2^LOGE: with v and sh known at compile
+// time (unrolled loops) this folds to one shift of tau (and an OR).  Twiddle
+// indexes stay in 32 bits (N <= 2^16).
+template <int LOGE>
+__device__ __forceinline__ uint32_t hi_bits(uint32_t tau, int v, int sh) {
+    return sh >= LOGE ? (tau >> (sh - LOGE)) : ((tau << (LOGE - sh)) | uint32_t(v >> sh));
+}
+
 // ------------------------------------------------------------------ forward
 
 template <int LOGR, int LOGE, bool WIDE>
@@ -102,8 +110,8 @@ __device__ __forceinline__ void fwd_cols_body(uint64_t (&x)[1 << LOGE], uint64_t
 #pragma unroll
         for (int v = 0; v < E; v++) {
             if (v & dist) continue;
-            const int rr = tau * E + v;
-            fwd_bfly<WIDE>(x[v], x[v + dist], w[(1 << st) + (rr >> (LOGR - st))], q);
+            const uint32_t idx = (1u << st) + hi_bits<LOGE>(uint32_t(tau), v, LOGR - st);
+            fwd_bfly<WIDE>(x[v], x[v + dist], w[idx], q);
         }
     }
 }
@@ -125,10 +133,13 @@ k_ntt_fwd_cols(const uint64_t *src, uint64_t *dst, const LimbMap map,
     const ulonglong2 *w = tw + size_t(p) * N;
     const int cl = threadIdx.x % CW, tau = threadIdx.x / CW;
     const size_t c = size_t(blockIdx.x) * CW + cl;
+    const uint32_t TS = uint32_t(T * S), SS = uint32_t(S);
+    const uint64_t *ip = in + c + size_t(tau) * S;
+    uint64_t *op = out + c + size_t(tau) * E * S;
 
     uint64_t x[E];
 #pragma unroll
-    for (int v = 0; v < E; v++) x[v] = in[c + size_t(tau + T * v) * S];
+    for (int v = 0; v < E; v++) x[v] = ip[uint32_t(v) * TS];
     // q < 2^58: no conditional subtractions; words leave below 4q + 2 LOGR q
     // and the row pass reduces them on load
     if (q < kWideBound)
@@ -136,23 +147,23 @@ k_ntt_fwd_cols(const uint64_t *src, uint64_t *dst, const LimbMap map,
     else
         fwd_cols_body<LOGR, LOGE, false>(x, sm, w, q, cl, tau);
 #pragma unroll
-    for (int v = 0; v < E; v++) out[c + size_t(tau * E + v) * S] = x[v];
+    for (int v = 0; v < E; v++) op[uint32_t(v) * SS] = x[v];
 }
 
 template <int LOGR, int LOGE, bool WIDE>
 __device__ __forceinline__ void fwd_rows_body(uint64_t (&x)[1 << LOGE], uint64_t *s,
-                                              const ulonglong2 *w, uint64_t q, int k1, size_t h,
+                                              const ulonglong2 *w, uint64_t q, int k1, uint32_t h,
                                               int tau) {
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E;
 #define PAD(u) ((u) + ((u) >> LOGE))
 #pragma unroll
     for (int st = 0; st < LOGE; st++) {
         const int half = E >> (st + 1);
+        const uint32_t base = (1u << (k1 + st)) + (h << st);
 #pragma unroll
         for (int v = 0; v < E; v++) {
             if (v & half) continue;
-            const size_t idx = (size_t(1) << (k1 + st)) + (h << st) + (v >> (LOGE - st));
-            fwd_bfly<WIDE>(x[v], x[v + half], w[idx], q);
+            fwd_bfly<WIDE>(x[v], x[v + half], w[base + uint32_t(v >> (LOGE - st))], q);
         }
     }
 #pragma unroll
@@ -163,11 +174,11 @@ __device__ __forceinline__ void fwd_rows_body(uint64_t (&x)[1 << LOGE], uint64_t
 #pragma unroll
     for (int st = LOGE; st < LOGR; st++) {
         const int dist = 1 << (LOGR - 1 - st);
+        const uint32_t base = (1u << (k1 + st)) + (h << st);
 #pragma unroll
         for (int v = 0; v < E; v++) {
             if (v & dist) continue;
-            const int u = tau * E + v;
-            const size_t idx = (size_t(1) << (k1 + st)) + (h << st) + (u >> (LOGR - st));
+            const uint32_t idx = base + hi_bits<LOGE>(uint32_t(tau), v, LOGR - st);
             fwd_bfly<WIDE>(x[v], x[v + dist], w[idx], q);
         }
     }
@@ -191,8 +202,8 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
     const ulonglong2 *w = tw + size_t(p) * N;
     const int k1 = log_n - LOGR;
     const int chl = threadIdx.x / T, tau = threadIdx.x % T;
-    const size_t h = size_t(blockIdx.x) * CC + chl;
-    uint64_t *base = out + h * R;
+    const uint32_t h = blockIdx.x * CC + chl;
+    uint64_t *base = out + size_t(h) * R;
     uint64_t *s = sm + chl * RP;
 #define PAD(u) ((u) + ((u) >> LOGE))
 
@@ -212,7 +223,7 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
         for (int v = 0; v < E; v++) base[tau + T * v] = s[PAD(tau + T * v)];
     } else {
         // ModDown combine: out = (y - lift) * D^-1 (+ add), lift now in NTT form
-        const size_t off = h * R;
+        const size_t off = size_t(h) * R;
         const uint64_t *yp = epi.y + (size_t(g) * epi.y_stride + epi.y_off[r]) * N + off;
         uint64_t *op = epi.out + (size_t(g) * epi.out_stride + epi.out_off[r]) * N + off;
         const uint64_t *ap =
@@ -248,13 +259,15 @@ k_ntt_inv_rows(const uint64_t *src, uint64_t *dst, const LimbMap map,
     const ulonglong2 *w = tw + size_t(p) * N;
     const int k1 = log_n - LOGR;
     const int chl = threadIdx.x / T, tau = threadIdx.x % T;
-    const size_t h = size_t(blockIdx.x) * CC + chl;
+    const uint32_t h = blockIdx.x * CC + chl;
+    const uint64_t *ib = in + size_t(h) * R;
+    uint64_t *ob = out + size_t(h) * R;
     uint64_t *s = sm + chl * RP;
 #define PAD(u) ((u) + ((u) >> LOGE))
 
     uint64_t x[E];
 #pragma unroll
-    for (int v = 0; v < E; v++) s[PAD(tau + T * v)] = in[h * R + tau + T * v];
+    for (int v = 0; v < E; v++) s[PAD(tau + T * v)] = ib[tau + T * v];
     __syncthreads();
 #pragma unroll
     for (int v = 0; v < E; v++) x[v] = s[PAD(tau * E + v)];
@@ -262,11 +275,11 @@ k_ntt_inv_rows(const uint64_t *src, uint64_t *dst, const LimbMap map,
 #pragma unroll
     for (int st = LOGR - 1; st >= LOGE; st--) {
         const int dist = 1 << (LOGR - 1 - st);
+        const uint32_t base = (1u << (k1 + st)) + (h << st);
 #pragma unroll
         for (int v = 0; v < E; v++) {
             if (v & dist) continue;
-            const int u = tau * E + v;
-            const size_t idx = (size_t(1) << (k1 + st)) + (h << st) + (u >> (LOGR - st));
+            const uint32_t idx = base + hi_bits<LOGE>(uint32_t(tau), v, LOGR - st);
             gs_bfly(x[v], x[v + dist], w[idx], q);
         }
     }
@@ -278,15 +291,15 @@ k_ntt_inv_rows(const uint64_t *src, uint64_t *dst, const LimbMap map,
 #pragma unroll
     for (int st = LOGE - 1; st >= 0; st--) {
         const int half = E >> (st + 1);
+        const uint32_t base = (1u << (k1 + st)) + (h << st);
 #pragma unroll
         for (int v = 0; v < E; v++) {
             if (v & half) continue;
-            const size_t idx = (size_t(1) << (k1 + st)) + (h << st) + (v >> (LOGE - st));
-            gs_bfly(x[v], x[v + half], w[idx], q);
+            gs_bfly(x[v], x[v + half], w[base + uint32_t(v >> (LOGE - st))], q);
         }
     }
 #pragma unroll
-    for (int v = 0; v < E; v++) out[h * R + tau + T * v] = x[v];
+    for (int v = 0; v < E; v++) ob[tau + T * v] = x[v];
 #undef PAD
 }
 
@@ -307,18 +320,21 @@ k_ntt_inv_cols(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
     const ulonglong2 *w = tw + size_t(p) * N;
     const int cl = threadIdx.x % CW, tau = threadIdx.x / CW;
     const size_t c = size_t(blockIdx.x) * CW + cl;
+    const uint32_t TS = uint32_t(T * S), SS = uint32_t(S);
+    uint64_t *ib = out + c + size_t(tau) * E * S;
+    uint64_t *ob = out + c + size_t(tau) * S;
 
     uint64_t x[E];
 #pragma unroll
-    for (int v = 0; v < E; v++) x[v] = out[c + size_t(tau * E + v) * S];
+    for (int v = 0; v < E; v++) x[v] = ib[uint32_t(v) * SS];
 #pragma unroll
     for (int st = LOGR - 1; st >= LOGE; st--) {
         const int dist = 1 << (LOGR - 1 - st);
 #pragma unroll
         for (int v = 0; v < E; v++) {
             if (v & dist) continue;
-            const int rr = tau * E + v;
-            gs_bfly(x[v], x[v + dist], w[(1 << st) + (rr >> (LOGR - st))], q);
+            const uint32_t idx = (1u << st) + hi_bits<LOGE>(uint32_t(tau), v, LOGR - st);
+            gs_bfly(x[v], x[v + dist], w[idx], q);
         }
     }
 #pragma unroll
@@ -346,7 +362,7 @@ k_ntt_inv_cols(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
         }
     }
 #pragma unroll
-    for (int v = 0; v < E; v++) out[c + size_t(tau + T * v) * S] = x[v];
+    for (int v = 0; v < E; v++) ob[uint32_t(v) * TS] = x[v];
 }
 
 // ------------------------------------------------------------------ launchers

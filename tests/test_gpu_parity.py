@@ -321,19 +321,55 @@ def test_integer_schemes_full_size(name):
 
 @pytest.mark.slow
 def test_ckks_n16_full_size():
-    """N = 2^16, L = 24, K = 4, dnum = 3: one pair through the fused op and a
-    rotation, checked limb for limb against the oracle."""
+    """N = 2^16, L = 24, K = 4, dnum = 3 in the benchmark's launch
+    configuration: the batch of 8 uniform pairs (the benchmark's seeds and
+    keys) through one fused HMult+relin+rescale launch, and HRotate(1) on the
+    batch; the first and last ciphertexts checked limb for limb against the
+    oracle."""
     p = W.PRESETS["ckks_n16"]
-    pr = Pair(p)
-    g = pr.g.galois_elt(1)
-    pr.gk.gen_galois(g)
-    pr.ok.gen_galois(g)
-    a, b = _uniform_pair(pr, p.L, 1, "full-ckks16")
-    da, db = pr.g.import_ct(a), pr.g.import_ct(b)
-    got = pr.g.export_ct(pr.g.mul_relin_rescale(pr.gk, da, db))[0]
-    assert np.array_equal(got, pr.o.rescale(pr.o.mul_relin(pr.ok, a[0], b[0])))
-    got = pr.g.export_ct(pr.g.rotate(pr.gk, da, g))[0]
-    assert np.array_equal(got, pr.o.rotate(pr.ok, a[0], g))
+    g_ctx, o_ctx = api.Context(p), octx_for(p)
+    gk, ok = g_ctx.keygen(W.seed_for("bench-keys")), o_ctx.keygen(W.seed_for("bench-keys"))
+    g = g_ctx.galois_elt(1)
+    gk.gen_galois(g)
+    ok.gen_galois(g)
+    seed = W.seed_for("bench-inputs")
+    a = torch.cat([g_ctx.ct_uniform(seed, 2 * i, p.L) for i in range(8)])
+    b = torch.cat([g_ctx.ct_uniform(seed, 2 * i + 1, p.L) for i in range(8)])
+    out = g_ctx.empty_ct(8, p.L - 1)
+    g_ctx.mul_relin_rescale(gk, a, b, out)
+    got = g_ctx.export_ct(out)
+    rot = g_ctx.export_ct(g_ctx.rotate(gk, a, g))
+    for i in (0, 7):
+        oa, ob = o_ctx.ct_uniform(seed, 2 * i, p.L), o_ctx.ct_uniform(seed, 2 * i + 1, p.L)
+        assert np.array_equal(got[i], o_ctx.rescale(o_ctx.mul_relin(ok, oa, ob))), i
+        assert np.array_equal(rot[i], o_ctx.rotate(ok, oa, g)), i
+
+
+def test_ckks_n16_noise_valid_accuracy():
+    """K = 8 special primes: decrypted slots of the batched HMult+relin+rescale
+    and of HRotate(1) within 2^-20 of the exact results, slots uniform in the
+    complex unit square at scale 2^50."""
+    from paper_2503_22227_gb300 import encoding
+    p = W.PRESETS["ckks_n16_k8"]
+    ctx = api.Context(p)
+    keys = ctx.keygen(W.seed_for("k8-accuracy"))
+    g = ctx.galois_elt(1)
+    keys.gen_galois(g)
+    n, scale = p.n, 2.0 ** 50
+    rng = W.rng_for("k8-accuracy")
+    zs = [(W.complex_slots(rng, n), W.complex_slots(rng, n)) for _ in range(4)]
+    a = torch.cat([ctx.encrypt(keys, encoding.encode(za, n, scale), W.seed_for(f"k8a{i}"))
+                   for i, (za, _) in enumerate(zs)])
+    b = torch.cat([ctx.encrypt(keys, encoding.encode(zb, n, scale), W.seed_for(f"k8b{i}"))
+                   for i, (_, zb) in enumerate(zs)])
+    prod = ctx.mul_relin_rescale(keys, a, b)
+    rot = ctx.rotate(keys, a, g)
+    s2 = scale * scale / ctx.q[-1]
+    for i, (za, zb) in enumerate(zs):
+        z = encoding.decode(ctx.decrypt(keys, prod[i:i + 1]), n, s2)
+        assert np.max(np.abs(z - za * zb)) < 2.0 ** -20, i
+        z = encoding.decode(ctx.decrypt(keys, rot[i:i + 1]), n, scale)
+        assert np.max(np.abs(z - np.roll(za, -1))) < 2.0 ** -20, i
 
 
 # ---------------------------------------------------------------- errors and edges
