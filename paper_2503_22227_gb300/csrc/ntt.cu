@@ -210,13 +210,17 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
     uint64_t x[E];
 #pragma unroll
     for (int v = 0; v < E; v++) x[v] = base[tau + T * v];
-    if (q < kWideBound) {  // the column pass left words below 2^64, not 4q
+    if (q < kWideBound) {
+        // no conditional subtractions in either pass: words stay below
+        // 4q + 2 log2(N) q <= 36q < 2^64, reduced once at the end
+        fwd_rows_body<LOGR, LOGE, true>(x, s, w, q, k1, h, tau);
 #pragma unroll
-        for (int v = 0; v < E; v++) x[v] = reduce_any(x[v], m);
+        for (int v = 0; v < E; v++) s[PAD(tau * E + v)] = reduce_any(x[v], m);
+    } else {
+        fwd_rows_body<LOGR, LOGE, false>(x, s, w, q, k1, h, tau);
+#pragma unroll
+        for (int v = 0; v < E; v++) s[PAD(tau * E + v)] = reduce4(x[v], q);
     }
-    fwd_rows_body<LOGR, LOGE, false>(x, s, w, q, k1, h, tau);
-#pragma unroll
-    for (int v = 0; v < E; v++) s[PAD(tau * E + v)] = reduce4(x[v], q);
     __syncthreads();
     if (!EPI) {
 #pragma unroll
