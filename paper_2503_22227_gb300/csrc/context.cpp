@@ -178,9 +178,23 @@ bool plan_fits_mont(const PlanSpec &s) {
     return sum < ((u128)1 << 64);
 }
 
+bool plan_fits_split(const PlanSpec &s) {
+    const uint64_t lim = uint64_t(1) << 60;
+    if (!plan_fits_mont(s) || s.src_mod.empty() || s.src_mod.size() > 8) return false;
+    for (uint64_t m : s.src_mod)
+        if (m >= lim) return false;
+    for (uint64_t p : s.dst_mod)
+        if (p == 0 || p >= lim) return false;
+    return true;
+}
+
+// A weight below 2^60 as its 30-bit halves, lo | hi << 32.
+static uint64_t split30(uint64_t c) { return (c & ((uint64_t(1) << 30) - 1)) | ((c >> 30) << 32); }
+
 std::vector<uint64_t> build_plan(const PlanSpec &s) {
     const uint32_t k = uint32_t(s.src_mod.size()), T = uint32_t(s.dst_mod.size());
     const bool mont = !s.exact && plan_fits_mont(s);
+    const bool split = mont && s.split && plan_fits_split(s);
     bool wrap = false;
     for (uint64_t q : s.dst_mod) wrap |= (q == 0);
     const auto &m = s.src_mod;
@@ -223,7 +237,8 @@ std::vector<uint64_t> build_plan(const PlanSpec &s) {
 
     std::vector<uint64_t> out(plan_words(k, T, mont), 0);
     out[0] = uint64_t(k) | (uint64_t(T) << 16) | (uint64_t(wrap ? 1 : 0) << 32) |
-             (uint64_t(s.lazy && !wrap ? 1 : 0) << 33) | (uint64_t(mont ? 1 : 0) << 34);
+             (uint64_t(s.lazy && !wrap ? 1 : 0) << 33) | (uint64_t(mont ? 1 : 0) << 34) |
+             (uint64_t(split ? 1 : 0) << 35);
     uint64_t *c = out.data() + 1;
     for (uint32_t i = 0; i < k; i++) c[i] = s.src_off[i];
     c += k;
@@ -261,6 +276,10 @@ std::vector<uint64_t> build_plan(const PlanSpec &s) {
             const uint64_t R = r64_mod(p), pr = h_mulmod(post[t], R, p);
             for (uint32_t i = 0; i < k; i++) Ct[size_t(i) * T + t] = h_mulmod(Wt[size_t(i) * T + t], pr, p);
             Mneg[t] = h_mulmod((p - Mt[t]) % p, pr, p);
+        }
+        if (split) {
+            for (size_t i = 0; i < size_t(k) * k; i++) C[i] = split30(C[i]);
+            for (size_t i = 0; i < size_t(k) * T; i++) Ct[i] = split30(Ct[i]);
         }
         return out;
     }
@@ -301,6 +320,7 @@ static PlanRef upload_plan(Context &c, const std::string &key, std::vector<uint6
     PlanRef ref;
     const size_t w = host.size();
     ref.mont = ((host[0] >> 34) & 1) != 0;
+    ref.split = ((host[0] >> 35) & 1) != 0;
     host.insert(host.end(), extra.begin(), extra.end());
     uint64_t *dev = nullptr;
     if (cudaMalloc(&dev, host.size() * 8) != cudaSuccess) return ref;
@@ -309,7 +329,7 @@ static PlanRef upload_plan(Context &c, const std::string &key, std::vector<uint6
         return ref;
     }
     c.plans[key] = dev;
-    c.plan_sizes[key] = uint32_t(w) | (ref.mont ? 0x80000000u : 0u);
+    c.plan_sizes[key] = uint32_t(w) | (ref.mont ? 0x80000000u : 0u) | (ref.split ? 0x40000000u : 0u);
     ref.p = dev;
     ref.words = uint32_t(w);
     return ref;
@@ -317,13 +337,14 @@ static PlanRef upload_plan(Context &c, const std::string &key, std::vector<uint6
 
 PlanRef get_plan_extra(Context &c, const std::string &key0, const PlanSpec &spec,
                        const std::vector<uint64_t> &extra) {
-    const std::string key = key0 + (spec.exact ? "/x" : "");
+    const std::string key = key0 + (spec.exact ? "/x" : spec.split ? "/s" : "");
     auto it = c.plans.find(key);
     if (it != c.plans.end()) {
         PlanRef ref;
         ref.p = it->second;
-        ref.words = c.plan_sizes[key] & 0x7fffffffu;
+        ref.words = c.plan_sizes[key] & 0x3fffffffu;
         ref.mont = (c.plan_sizes[key] & 0x80000000u) != 0;
+        ref.split = (c.plan_sizes[key] & 0x40000000u) != 0;
         return ref;
     }
     return upload_plan(c, key, build_plan(spec), extra);

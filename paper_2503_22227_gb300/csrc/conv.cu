@@ -241,6 +241,112 @@ __device__ __forceinline__ uint64_t eval_mont(const uint64_t (&a)[KMAX], bool gt
     return P.lazy ? r : csub(r, p);
 }
 
+// ================================================================== split weights
+
+// Montgomery layout with k <= 8 and every modulus below 2^60: digits and
+// weights are split into 30-bit halves, x = xh 2^30 + xl, and a sum of
+// products is kept as three 64-bit accumulators
+//   ll = sum xl wl,  mm = sum (xl wh + xh wl),  hh = sum xh wh,
+// each term one 32 x 32 -> 64-bit multiply-add.  With at most 8 products per
+// sum, ll and hh stay below 2^63 and mm below 16 (2^30 - 1)^2 < 2^64; the
+// value ll + mm 2^30 + hh 2^60 is the same exact sum as in the Montgomery
+// layout (below 2^64 times the modulus), joined into 128 bits and reduced by
+// one Montgomery reduction.
+
+struct Acc3 {
+    uint64_t ll, mm, hh;
+};
+
+__device__ __forceinline__ void mac3(Acc3 &a, uint32_t xl, uint32_t xh, uint64_t w) {
+    const uint32_t wl = uint32_t(w), wh = uint32_t(w >> 32);
+    a.ll += uint64_t(xl) * wl;
+    a.mm += uint64_t(xl) * wh;
+    a.mm += uint64_t(xh) * wl;
+    a.hh += uint64_t(xh) * wh;
+}
+
+__device__ __forceinline__ U128 join3(const Acc3 &a) {
+    U128 x;
+    asm("add.cc.u64 %0, %2, %3;\n\t"
+        "addc.u64 %1, %4, 0;"
+        : "=l"(x.lo), "=l"(x.hi)
+        : "l"(a.ll), "l"(a.mm << 30), "l"(a.mm >> 34));
+    asm("add.cc.u64 %0, %0, %2;\n\t"
+        "addc.u64 %1, %1, %3;"
+        : "+l"(x.lo), "+l"(x.hi)
+        : "l"(a.hh << 60), "l"(a.hh >> 4));
+    return x;
+}
+
+constexpr uint32_t kMask30 = (1u << 30) - 1;
+
+// Mixed-radix digits as 30-bit halves, and the centring decision (the
+// lexicographic comparison with the digits of (M-1)/2 runs from the least
+// significant digit up: the last differing digit decides).
+template <int KMAX>
+__device__ __forceinline__ bool mixed_radix_split(const uint64_t (&r)[KMAX], uint32_t (&al)[KMAX],
+                                                  uint32_t (&ah)[KMAX], const MontView &P) {
+    bool gt = false;
+#pragma unroll
+    for (int j = 0; j < KMAX; j++) {
+        al[j] = ah[j] = 0;
+        if (uint32_t(j) < P.k) {
+            Acc3 acc{0, 0, 0};
+            mac3(acc, uint32_t(r[j]) & kMask30, uint32_t(r[j] >> 30), P.C[size_t(j) * P.k + j]);
+#pragma unroll
+            for (int i = 0; i < KMAX; i++)
+                if (i < j) mac3(acc, al[i], ah[i], P.C[size_t(i) * P.k + j]);
+            const uint64_t mj = P.smod[2 * j];
+            const uint64_t aj = csub(redc(join3(acc), mj, P.smod[2 * j + 1]), mj);
+            al[j] = uint32_t(aj) & kMask30;
+            ah[j] = uint32_t(aj >> 30);
+            if (aj != P.h[j]) gt = aj > P.h[j];
+        }
+    }
+    return gt;
+}
+
+// Targets t and t+1 (two independent chains).
+template <int KMAX>
+__device__ __forceinline__ void eval_split2(const uint32_t (&al)[KMAX], const uint32_t (&ah)[KMAX],
+                                            bool gt, const MontView &P, uint32_t t, uint64_t &r0,
+                                            uint64_t &r1) {
+    const uint32_t T = P.T;
+    Acc3 a0{0, 0, 0}, a1{0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < KMAX; i++) {
+        if (uint32_t(i) < P.k) {
+            mac3(a0, al[i], ah[i], P.Ct[size_t(i) * T + t]);
+            mac3(a1, al[i], ah[i], P.Ct[size_t(i) * T + t + 1]);
+        }
+    }
+    if (gt) {  // below 2^60 each: ll stays below 2^64
+        a0.ll += P.Mneg[t];
+        a1.ll += P.Mneg[t + 1];
+    }
+    const uint64_t p0 = P.dmod[2 * t], p1 = P.dmod[2 * t + 2];
+    r0 = redc(join3(a0), p0, P.dmod[2 * t + 1]);
+    r1 = redc(join3(a1), p1, P.dmod[2 * t + 3]);
+    if (!P.lazy) {
+        r0 = csub(r0, p0);
+        r1 = csub(r1, p1);
+    }
+}
+
+template <int KMAX>
+__device__ __forceinline__ uint64_t eval_split(const uint32_t (&al)[KMAX],
+                                               const uint32_t (&ah)[KMAX], bool gt,
+                                               const MontView &P, uint32_t t) {
+    Acc3 a{0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < KMAX; i++)
+        if (uint32_t(i) < P.k) mac3(a, al[i], ah[i], P.Ct[size_t(i) * P.T + t]);
+    if (gt) a.ll += P.Mneg[t];
+    const uint64_t p = P.dmod[2 * t];
+    const uint64_t r = redc(join3(a), p, P.dmod[2 * t + 1]);
+    return P.lazy ? r : csub(r, p);
+}
+
 // ================================================================== kernels
 
 template <int KMAX>
@@ -251,7 +357,7 @@ __device__ __forceinline__ void load_sources(uint64_t (&a)[KMAX], uint32_t k,
     for (int i = 0; i < KMAX; i++) a[i] = uint32_t(i) < k ? s[src_off[i] * n + x] : 0;
 }
 
-template <int KMAX, bool MONT>
+template <int KMAX, bool MONT, bool SPLIT = false>
 __global__ void __launch_bounds__(256, 4)
 k_conv(const PlanList plans, const uint64_t *__restrict__ src, size_t src_item, size_t src_plan,
        uint64_t *__restrict__ dst, size_t dst_item, size_t dst_plan, uint32_t log_n) {
@@ -262,7 +368,24 @@ k_conv(const PlanList plans, const uint64_t *__restrict__ src, size_t src_item, 
     const size_t n = size_t(1) << log_n;
     const uint64_t *s = src + blockIdx.y * src_item + blockIdx.z * src_plan;
     uint64_t *d = dst + blockIdx.y * dst_item + blockIdx.z * dst_plan;
-    if (MONT) {
+    if (SPLIT) {
+        const MontView P = mont_view(splan);
+        for (size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
+             x += size_t(gridDim.x) * blockDim.x) {
+            uint64_t r[KMAX];
+            load_sources<KMAX>(r, P.k, P.src_off, s, x, n);
+            uint32_t al[KMAX], ah[KMAX];
+            const bool gt = mixed_radix_split<KMAX>(r, al, ah, P);
+            uint32_t t = 0;
+            for (; t + 1 < P.T; t += 2) {
+                uint64_t r0, r1;
+                eval_split2<KMAX>(al, ah, gt, P, t, r0, r1);
+                d[P.dst_off[t] * n + x] = r0;
+                d[P.dst_off[t + 1] * n + x] = r1;
+            }
+            if (t < P.T) d[P.dst_off[t] * n + x] = eval_split<KMAX>(al, ah, gt, P, t);
+        }
+    } else if (MONT) {
         const MontView P = mont_view(splan);
         for (size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
              x += size_t(gridDim.x) * blockDim.x) {
@@ -361,7 +484,15 @@ int launch_conv(const Context &c, const PlanList &plans, const uint64_t *src, si
     const size_t n = c.n;
     dim3 grid(unsigned((n + 1023) / 1024), items, plans.n);
     const size_t sm = size_t(plans.words) * 8;
-    if (plans.mont)
+    if (plans.split) {
+        if (plans.kmax > 8) return CATFHE_EINVAL;
+        if (plans.kmax <= 4)
+            k_conv<4, true, true><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst,
+                                                        dst_item, dst_plan, c.log_n);
+        else
+            k_conv<8, true, true><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst,
+                                                        dst_item, dst_plan, c.log_n);
+    } else if (plans.mont)
         run_conv<true>(pick_kmax(plans.kmax), grid, sm, s, plans, src, src_item, src_plan, dst,
                        dst_item, dst_plan, c.log_n);
     else

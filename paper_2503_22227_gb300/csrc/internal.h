@@ -43,9 +43,11 @@ struct LimbMap {
 // Constants of one exact, centred base conversion from k source moduli to T
 // target moduli (mixed-radix form of the CRT; see conv.cu), packed into a
 // flat array of 64-bit words.  Word 0 is the header
-//   k | T << 16 | wrap64 << 32 | lazy << 33 | mont << 34
+//   k | T << 16 | wrap64 << 32 | lazy << 33 | mont << 34 | split << 35
 // (wrap64: targets are 2^64; lazy: outputs may lie in [0, 2q) instead of
-// [0, q), for an NTT to consume; mont: the Montgomery layout below).
+// [0, q), for an NTT to consume; mont: the Montgomery layout below; split:
+// the same layout with every weight of C and Ct stored as its two 30-bit
+// halves lo | hi << 32, for k <= 8 and moduli below 2^60).
 // Then src_off[k], dst_off[T] (limb offsets per item) and
 //  exact layout:  smod[k][4] (q, 2^64 mod q, its Shoup quotient, floor(2^64/q)),
 //                 dmod[T][4], pre[k], pre_s[k], W[k][k] (prod_{l<i} m_l mod m_j),
@@ -73,6 +75,7 @@ __host__ __device__ inline size_t plan_words(uint64_t header) {
 struct PlanSpec {
     bool lazy = false;
     bool exact = false;  // force the exact layout (else Montgomery when it fits)
+    bool split = false;  // Montgomery with split weights (when it fits)
     std::vector<uint64_t> src_mod;
     std::vector<uint32_t> src_off;
     std::vector<uint64_t> pre;
@@ -84,10 +87,15 @@ std::vector<uint64_t> build_plan(const PlanSpec &s);
 // The Montgomery layout needs sum(src_mod) + 1 < 2^64 (every accumulated sum
 // stays below 2^64 times its modulus).
 bool plan_fits_mont(const PlanSpec &s);
+// Split weights need k <= 8 and every source and target modulus in (0, 2^60)
+// (then the 30-bit half products of a sum accumulate below 2^64), besides
+// the Montgomery bound.
+bool plan_fits_split(const PlanSpec &s);
 struct PlanRef {
     const uint64_t *p = nullptr;  // device copy
     uint32_t words = 0;
     bool mont = false;
+    bool split = false;
 };
 struct Context;
 PlanRef get_plan(Context &c, const std::string &key, const PlanSpec &spec);
@@ -101,6 +109,7 @@ struct PlanList {
     uint32_t kmax;   // largest source count among them
     uint32_t words;  // largest packed size among them
     uint32_t mont;   // all plans use the Montgomery layout
+    uint32_t split;  // ... with split weights
 };
 
 // Host-side prime record.

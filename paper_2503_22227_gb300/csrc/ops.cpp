@@ -53,19 +53,26 @@ static int get_ws(Context &c, void *ws, size_t ws_bytes, size_t need, char **out
     return CATFHE_OK;
 }
 
-// One launch's plans, all in one layout: Montgomery when every plan fits it.
+// One launch's plans, all in one layout: Montgomery when every plan fits it
+// (with split weights when every plan fits those too), else exact.
 static int make_list(Context &c, const std::vector<std::pair<std::string, PlanSpec>> &specs,
                      PlanList &pl) {
-    bool all = true;
-    for (const auto &s : specs) all = all && plan_fits_mont(s.second);
+    bool all = true, all_split = true;
+    for (const auto &s : specs) {
+        all = all && plan_fits_mont(s.second);
+        all_split = all_split && plan_fits_split(s.second);
+    }
     pl = PlanList{};
     pl.n = uint32_t(specs.size());
     pl.mont = all ? 1 : 0;
+    pl.split = all && all_split ? 1 : 0;
     for (size_t i = 0; i < specs.size(); i++) {
         PlanSpec sp = specs[i].second;
         sp.exact = !all;
+        sp.split = pl.split != 0;
         const PlanRef r = get_plan(c, specs[i].first, sp);
         if (!r.p) return CATFHE_ENOMEM;
+        if (r.mont != (pl.mont != 0) || r.split != (pl.split != 0)) return CATFHE_EINVAL;
         pl.p[i] = r.p;
         pl.kmax = std::max<uint32_t>(pl.kmax, uint32_t(sp.src_mod.size()));
         pl.words = std::max(pl.words, r.words);
