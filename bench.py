@@ -340,6 +340,32 @@ def serving_sweep(W, fracs=(0.1, 0.5, 0.8, 1.5), lanes=8, max_active=64):
     return out
 
 
+NTT_TRAFFIC = os.path.join(ROOT, "profiles", "ntt_fwd_ckks_n16_384limbs.md")
+NTT_SOURCE = os.path.join(ROOT, "paper_2503_22227_gb300", "csrc", "ntt.cu")
+
+
+def ntt_traffic():
+    """DRAM bytes per forward transform of the 384 limbs (both passes), from
+    the committed ncu summary, if it was taken on the current NTT source."""
+    import hashlib
+    try:
+        text = open(NTT_TRAFFIC).read()
+        src = hashlib.sha256(open(NTT_SOURCE, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    fields = {}
+    for line in text.splitlines():
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    if fields.get("ntt.cu sha256") != src:
+        return None
+    try:
+        return int(fields["traffic bytes per transform"])
+    except (KeyError, ValueError):
+        return None
+
+
 def run_catfhe(args):
     import numpy as np
     import torch
@@ -414,11 +440,13 @@ def run_catfhe(args):
     torch.cuda.synchronize()
     reps = 20
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("ntt_roofline")
     f0.record(stream)
     for _ in range(reps):
         ctx.ntt(limbs)
     f1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     ntt_s = f0.elapsed_time(f1) * 1e-3 / reps
     n_limbs = 2 * BATCH * L
     bfly = n_limbs * (p.n // 2) * 16
@@ -495,7 +523,7 @@ def run_catfhe(args):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "kernel": "batched forward NTT (k_ntt_fwd_cols + k_ntt_fwd_rows)",
                      "achieved": ntt_rate / 1e9, "peak": bf_peak / 1e9, "unit": "Gbutterfly/s",
-                     "frac": ntt_rate / bf_peak, "traffic": None,
+                     "frac": ntt_rate / bf_peak, "traffic": ntt_traffic(),
                      "peak_source": "measured: register-resident Shoup butterfly loop "
                                     "(catfhe_measure_int_peak), whole GPU",
                      "hbm_view": {"achieved_gbs": ntt_gbs, "peak_gbs": hbm / 1e9,

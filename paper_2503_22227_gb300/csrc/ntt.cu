@@ -74,6 +74,25 @@ __device__ __forceinline__ uint64_t reduce_any(uint64_t x, const DevMod &m) {
 
 constexpr uint64_t kWideBound = uint64_t(1) << 58;
 
+// Limb of this CTA: group g (ciphertext or polynomial) and position r within
+// the map's period.  PRIME_MAJOR (used by the forward transform, where it
+// measured faster; the inverse is faster the other way): when the launch
+// covers whole groups, consecutive blockIdx.y walk over the groups at one
+// position (one prime), so the CTAs that read one prime's twiddle table run
+// back to back and find it in L2.
+template <bool PRIME_MAJOR>
+__device__ __forceinline__ void limb_of(const LimbMap &map, uint32_t &g, uint32_t &r) {
+    const uint32_t y = blockIdx.y, Y = gridDim.y;
+    if (PRIME_MAJOR && Y % map.period == 0) {
+        const uint32_t G = Y / map.period;
+        g = y % G;
+        r = y / G;
+    } else {
+        g = y / map.period;
+        r = y % map.period;
+    }
+}
+
 // (tau E + v) >> sh for 0 <= v < E = 2^LOGE: with v and sh known at compile
 // time (unrolled loops) this folds to one shift of tau (and an OR).  Twiddle
 // indexes stay in 32 bits (N <= 2^16).
@@ -122,8 +141,8 @@ k_ntt_fwd_cols(const uint64_t *src, uint64_t *dst, const LimbMap map,
                const DevMod *__restrict__ mods, const ulonglong2 *__restrict__ tw, int log_n) {
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CW = 256 / T;
     __shared__ uint64_t sm[R * CW];
-    const uint32_t limb = blockIdx.y;
-    const uint32_t g = limb / map.period, r = limb % map.period;
+    uint32_t g, r;
+    limb_of<true>(map, g, r);
     const size_t N = size_t(1) << log_n;
     const size_t S = N >> LOGR;
     const uint64_t *in = src + (size_t(g) * map.src_stride + map.src_off[r]) * N;
@@ -192,8 +211,8 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CC = 256 / T;
     constexpr int RP = R + R / E;
     __shared__ uint64_t sm[CC * RP];
-    const uint32_t limb = blockIdx.y;
-    const uint32_t g = limb / map.period, r = limb % map.period;
+    uint32_t g, r;
+    limb_of<true>(map, g, r);
     const size_t N = size_t(1) << log_n;
     uint64_t *out = data + (size_t(g) * map.dst_stride + map.dst_off[r]) * N;
     const int p = map.prime[r];
@@ -253,8 +272,8 @@ k_ntt_inv_rows(const uint64_t *src, uint64_t *dst, const LimbMap map,
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CC = 256 / T;
     constexpr int RP = R + R / E;
     __shared__ uint64_t sm[CC * RP];
-    const uint32_t limb = blockIdx.y;
-    const uint32_t g = limb / map.period, r = limb % map.period;
+    uint32_t g, r;
+    limb_of<false>(map, g, r);
     const size_t N = size_t(1) << log_n;
     const uint64_t *in = src + (size_t(g) * map.src_stride + map.src_off[r]) * N;
     uint64_t *out = dst + (size_t(g) * map.dst_stride + map.dst_off[r]) * N;
@@ -313,8 +332,8 @@ k_ntt_inv_cols(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
                const ulonglong2 *__restrict__ tw, int log_n) {
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CW = 256 / T;
     __shared__ uint64_t sm[R * CW];
-    const uint32_t limb = blockIdx.y;
-    const uint32_t g = limb / map.period, r = limb % map.period;
+    uint32_t g, r;
+    limb_of<false>(map, g, r);
     const size_t N = size_t(1) << log_n;
     const size_t S = N >> LOGR;
     uint64_t *out = data + (size_t(g) * map.dst_stride + map.dst_off[r]) * N;
