@@ -271,6 +271,12 @@ def secondary(ctx, keys, a, api, W):
     t = _time(rotate_all, 5)
     out["hrotate_r1_16"] = {"value": a.shape[0] * len(gs) / t, "unit": "HRotate/s",
                             "note": "8 ciphertexts at level 24, r = 1..16 (16 Galois keys)"}
+    hoisted = torch.empty((len(gs),) + tuple(a.shape), dtype=a.dtype, device=a.device)
+    th = _time(lambda: ctx.rotate_hoisted(keys, a, gs, hoisted), 5)
+    out["hrotate_r1_16_hoisted"] = {
+        "value": a.shape[0] * len(gs) / th, "unit": "HRotate/s",
+        "note": "the same 128 rotations with one shared ModUp per ciphertext "
+                "(catfhe_rotate_hoisted; outputs equal catfhe_rotate bit for bit)"}
     for name in ("bfv_n14", "bgv_n14"):
         p = W.PRESETS[name]
         c2 = api.Context(p)

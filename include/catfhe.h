@@ -75,7 +75,11 @@ enum {
     CATFHE_OP_SUB = 9,
     CATFHE_OP_MUL_INT = 10,
     CATFHE_OP_ADD_CONST = 11,
-    CATFHE_OP_DROP = 12
+    CATFHE_OP_DROP = 12,
+    /* workspace of catfhe_rotate_hoisted (any number of rotations) */
+    CATFHE_OP_ROTATE_HOISTED = 13,
+    /* batch entry: out = a * plaintext b (catfhe_mul_plain; no workspace) */
+    CATFHE_OP_MUL_PLAIN = 14
 };
 
 /* Forms for catfhe_ct_import / catfhe_ct_export. */
@@ -222,6 +226,22 @@ int catfhe_mul_int(catfhe_ctx *ctx, const uint64_t *a, int64_t k, uint64_t *out,
 int catfhe_add_const(catfhe_ctx *ctx, const uint64_t *a, int64_t k, uint64_t *out,
                      uint32_t level, uint32_t count, void *stream);
 
+/* A plaintext polynomial for catfhe_mul_plain (Table 1 "multiply_plain"):
+ * host int64[N] signed coefficients (CKKS: the encoded, scaled message;
+ * BGV: a polynomial mod t) reduced mod q_0 .. q_{level-1} into the device
+ * buffer pt u64[level][N], in NTT form.  ESCHEME for BFV.  Synchronises on
+ * the host copy. */
+int catfhe_plain_import(catfhe_ctx *ctx, const int64_t *coeffs, uint32_t level, uint64_t *pt,
+                        void *stream);
+
+/* Multiplication by a plaintext (Table 1 "multiply_plain"): both
+ * polynomials times pt, limb by limb in NTT form; pt u64[>= level][N] from
+ * catfhe_plain_import (its first `level` limbs are used).  No relinearisation;
+ * a CKKS product carries the scale of a times the plaintext's scale.
+ * ESCHEME for BFV. */
+int catfhe_mul_plain(catfhe_ctx *ctx, const uint64_t *a, const uint64_t *pt, uint64_t *out,
+                     uint32_t level, uint32_t count, void *stream);
+
 /* Keeps primes q_0 .. q_{new_level-1}: out is u64[count][2][new_level][N]
  * (CKKS scale and plaintext unchanged); out must not alias a. */
 int catfhe_drop_level(catfhe_ctx *ctx, const uint64_t *a, uint32_t level, uint32_t new_level,
@@ -233,6 +253,22 @@ int catfhe_drop_level(catfhe_ctx *ctx, const uint64_t *a, uint32_t level, uint32
 int catfhe_rotate(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
                   uint64_t galois_elt, uint64_t *out, uint32_t level, uint32_t count,
                   void *ws, size_t ws_bytes, void *stream);
+
+/* Several rotations of the same ciphertexts with one shared ModUp (Table 1
+ * "rotate_vector_random" over many steps; hoisting): the exact lift of each
+ * digit of a1 commutes with sigma_g (a signed permutation of coefficients;
+ * the centred lift is odd), so ModUp(sigma_g(a1)) = sigma_g(ModUp(a1)) and
+ * each rotation only permutes the lifted digits, then runs the inner product
+ * and ModDown.  out[r] = catfhe_rotate(a, galois_elts[r]) bit for bit, for
+ * r < n_rot; out is u64[n_rot][count][2][level][N].  CKKS and BGV (ESCHEME
+ * for BFV); every key is checked (ENOKEY) before anything is enqueued.
+ * Workspace: catfhe_workspace_bytes(CATFHE_OP_ROTATE_HOISTED, level, count),
+ * independent of n_rot.  galois_elts is host memory; with n_rot = 0 nothing
+ * is read or written (out may be NULL). */
+int catfhe_rotate_hoisted(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
+                          const uint64_t *galois_elts, uint32_t n_rot, uint64_t *out,
+                          uint32_t level, uint32_t count, void *ws, size_t ws_bytes,
+                          void *stream);
 
 /* CKKS rescale round(c / q_{l-1}) (Table 1 "rescale"), or BGV modulus
  * switch (c - d) / q_{l-1}, d = t [c t^-1]_{q_{l-1}} (the plaintext then
@@ -302,7 +338,8 @@ uint64_t catfhe_kernel_launches(void);
  * they use: CATFHE_OP_MUL_RELIN, _MUL_RELIN_RESCALE (keys, a, b, out);
  * _ROTATE (keys, a, out, arg = Galois element); _RESCALE (a, out);
  * _ADD, _SUB (a, b, out); _MUL_INT, _ADD_CONST (a, out, arg = the int64
- * constant as two's complement); _DROP (a, out, level_out). */
+ * constant as two's complement); _DROP (a, out, level_out); _MUL_PLAIN
+ * (a, b = plaintext from catfhe_plain_import, out). */
 typedef struct {
     int32_t op;
     uint32_t level;

@@ -108,6 +108,7 @@ def lib():
                 "oc_mul_int": (None, [ctypes.c_void_p, u64p, ctypes.c_int64, u64p, ctypes.c_int]),
                 "oc_add_const": (None, [ctypes.c_void_p, u64p, ctypes.c_int64, u64p, ctypes.c_int]),
                 "oc_drop": (None, [ctypes.c_void_p, u64p, ctypes.c_int, ctypes.c_int, u64p]),
+                "oc_mul_plain": (None, [ctypes.c_void_p, u64p, i64p, u64p, ctypes.c_int]),
                 "oc_keyswitch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, u64p, ctypes.c_int,
                                                 ctypes.c_uint64, u64p]),
                 "oc_rescale": (None, [ctypes.c_void_p, u64p, u64p, ctypes.c_int]),
@@ -337,6 +338,13 @@ class Context:
         a = np.ascontiguousarray(a, dtype=np.uint64)
         out = np.zeros((2, new_level, self.n), dtype=np.uint64)
         lib().oc_drop(self._h, _u64(a), a.shape[1], new_level, _u64(out))
+        return out
+
+    def mul_plain(self, a, pt):
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        pt = np.ascontiguousarray(pt, dtype=np.int64)
+        out = np.zeros_like(a)
+        lib().oc_mul_plain(self._h, _u64(a), _i64(pt), _u64(out), a.shape[1])
         return out
 
     def tensor(self, a, b):

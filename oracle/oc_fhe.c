@@ -505,6 +505,24 @@ void oc_add_const(const void *ctx, const uint64_t *a, int64_t k, uint64_t *out, 
         out[(size_t)i * n] = oc_addmod(a[(size_t)i * n], oc_reduce_i64(k, c->q[i]), c->q[i]);
 }
 
+/* Multiplication by a plaintext polynomial (Table 1 "multiply_plain"): each
+ * polynomial of the ciphertext times pt (signed coefficients reduced mod
+ * q_i), a negacyclic product per limb. */
+void oc_mul_plain(const void *ctx, const uint64_t *a, const int64_t *pt, uint64_t *out, int level) {
+    const oc_ctx *c = ctx;
+    uint64_t n = c->n;
+    uint64_t *pi = malloc(sizeof(uint64_t) * n);
+    for (int i = 0; i < level; i++) {
+        uint64_t m = c->q[i];
+        for (uint64_t j = 0; j < n; j++) pi[j] = oc_reduce_i64(pt[j], m);
+        for (int p = 0; p < 2; p++) {
+            size_t o = ((size_t)p * (size_t)level + (size_t)i) * n;
+            oc_negacyclic_mul(out + o, a + o, pi, c->log_n, m, c->psi_q[i]);
+        }
+    }
+    free(pi);
+}
+
 /* Level drop: keeps the limbs of q_0 .. q_{new_level-1} of each polynomial. */
 void oc_drop(const void *ctx, const uint64_t *a, int level, int new_level, uint64_t *out) {
     const oc_ctx *c = ctx;

@@ -22,6 +22,8 @@ LIB_PATH = os.path.join(_PKG, "libcatfhe.so")
 CKKS, BFV, BGV = 0, 1, 2
 OP_MUL_RELIN, OP_MUL_RELIN_RESCALE, OP_ROTATE, OP_RESCALE, OP_DECRYPT, OP_EXPORT, OP_NTT = range(1, 8)
 OP_ADD, OP_SUB, OP_MUL_INT, OP_ADD_CONST, OP_DROP = range(8, 13)
+OP_ROTATE_HOISTED = 13
+OP_MUL_PLAIN = 14
 FORM_COEFF, FORM_NATIVE = 0, 1
 FORM_ASYNC = 0x100      # OR-ed into a form: import / export without synchronising
 
@@ -37,6 +39,7 @@ EXPORTS = [
     "catfhe_batch_capture", "catfhe_graph_launch", "catfhe_graph_nodes", "catfhe_graph_destroy",
     "catfhe_tune_ntt", "catfhe_ntt_schedule", "catfhe_set_ntt_schedule",
     "catfhe_sub", "catfhe_mul_int", "catfhe_add_const", "catfhe_drop_level",
+    "catfhe_rotate_hoisted", "catfhe_plain_import", "catfhe_mul_plain",
 ]
 
 
@@ -101,6 +104,9 @@ def load(path: str = LIB_PATH):
             "catfhe_mul_relin": (ctypes.c_int, [vp, vp, vp, vp, vp, u32, u32, vp, sz, vp]),
             "catfhe_mul_relin_rescale": (ctypes.c_int, [vp, vp, vp, vp, vp, u32, u32, vp, sz, vp]),
             "catfhe_rotate": (ctypes.c_int, [vp, vp, vp, u64, vp, u32, u32, vp, sz, vp]),
+            "catfhe_rotate_hoisted": (ctypes.c_int, [vp, vp, vp, vp, u32, vp, u32, u32, vp, sz, vp]),
+            "catfhe_plain_import": (ctypes.c_int, [vp, vp, u32, vp, vp]),
+            "catfhe_mul_plain": (ctypes.c_int, [vp, vp, vp, vp, u32, u32, vp]),
             "catfhe_rescale": (ctypes.c_int, [vp, vp, vp, u32, u32, vp, sz, vp]),
             "catfhe_decrypt": (ctypes.c_int, [vp, vp, vp, u32, u64, vp, vp, sz, vp]),
             "catfhe_ntt": (ctypes.c_int, [vp, vp, u32, u32, ctypes.c_int, vp]),
@@ -348,6 +354,39 @@ class Context:
                                     _ptr(ws), ws.numel(), _stream()), "catfhe_rotate")
         return out
 
+    def plain_import(self, coeffs, level: int | None = None):
+        """Signed plaintext coefficients (int64[N]) -> device plaintext
+        [level][N] in NTT form, for mul_plain."""
+        level = self.L if level is None else level
+        m = np.ascontiguousarray(np.asarray(coeffs, dtype=np.int64))
+        assert m.shape == (self.n,)
+        torch = _torch()
+        pt = torch.empty((level, self.n), dtype=torch.int64, device="cuda")
+        _check(load().catfhe_plain_import(self._h, m.ctypes.data_as(vp), level, _ptr(pt), _stream()),
+               "catfhe_plain_import")
+        return pt
+
+    def mul_plain(self, a, pt, out=None):
+        count, _, level, _ = a.shape
+        out = self.empty_ct(count, level) if out is None else out
+        _check(load().catfhe_mul_plain(self._h, _ptr(a), _ptr(pt), _ptr(out), level, count,
+                                       _stream()), "catfhe_mul_plain")
+        return out
+
+    def rotate_hoisted(self, keys: "Keys", a, galois_elts, out=None):
+        """Rotations of the same ciphertexts by every Galois element, one
+        shared ModUp: returns (or fills) [n_rot][count][2][level][N]."""
+        count, _, level, n = a.shape
+        gs = np.ascontiguousarray(np.asarray(galois_elts, dtype=np.uint64))
+        torch = _torch()
+        if out is None:
+            out = torch.empty((len(gs), count, 2, level, n), dtype=torch.int64, device="cuda")
+        ws = self.workspace(OP_ROTATE_HOISTED, level, count)
+        _check(load().catfhe_rotate_hoisted(self._h, keys._h, _ptr(a), gs.ctypes.data_as(vp),
+                                            len(gs), _ptr(out), level, count, _ptr(ws), ws.numel(),
+                                            _stream()), "catfhe_rotate_hoisted")
+        return out
+
     def rescale(self, a, out=None):
         count, _, level, _ = a.shape
         out = self.empty_ct(count, level - 1) if out is None else out
@@ -406,8 +445,9 @@ def kernel_launches() -> int:
 def make_op(kind: int, ctx: "Context", a, out, keys: "Keys" = None, b=None, galois_elt: int = 0,
             const: int = 0) -> Op:
     """An entry of an uneven batch: `a`, `b`, `out` are device tensors
-    [count][2][level][N] of ctx's ring degree.  galois_elt for rotations,
-    const (int64) for MUL_INT / ADD_CONST; DROP takes the level of `out`."""
+    [count][2][level][N] of ctx's ring degree (for MUL_PLAIN `b` is a
+    plaintext from plain_import).  galois_elt for rotations, const (int64)
+    for MUL_INT / ADD_CONST; DROP takes the level of `out`."""
     o = Op()
     o.op = kind
     o.count, _, o.level, _ = a.shape

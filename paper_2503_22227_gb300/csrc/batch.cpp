@@ -37,6 +37,8 @@ int op_add_const(Context &c, const uint64_t *a, int64_t k, uint64_t *out, uint32
                  uint32_t count, cudaStream_t s);
 int op_drop_level(Context &c, const uint64_t *a, uint32_t level, uint32_t new_level,
                   uint64_t *out, uint32_t count, cudaStream_t s);
+int op_mul_plain(Context &c, const uint64_t *a, const uint64_t *pt, uint64_t *out, uint32_t level,
+                 uint32_t count, cudaStream_t s);
 
 namespace {
 
@@ -109,6 +111,9 @@ int check_op(const catfhe_op &o) {
         case CATFHE_OP_DROP:
             return (o.level_out >= 1 && o.level_out <= o.level && o.a != o.out) ? CATFHE_OK
                                                                             : CATFHE_ELEVEL;
+        case CATFHE_OP_MUL_PLAIN:
+            if (!o.b) return CATFHE_EINVAL;
+            return c.scheme == CATFHE_BFV ? CATFHE_ESCHEME : CATFHE_OK;
         default:
             return CATFHE_EINVAL;
     }
@@ -190,6 +195,8 @@ int run_one(const catfhe_op &o, void *ws, size_t ws_bytes_in, cudaStream_t s) {
             return op_add_const(c, o.a, int64_t(o.arg), o.out, o.level, o.count, s);
         case CATFHE_OP_DROP:
             return op_drop_level(c, o.a, o.level, o.level_out, o.out, o.count, s);
+        case CATFHE_OP_MUL_PLAIN:
+            return op_mul_plain(c, o.a, o.b, o.out, o.level, o.count, s);
         default:
             return CATFHE_EINVAL;
     }

@@ -15,6 +15,13 @@ int op_mul_relin(Context &c, const Keys &keys, const uint64_t *a, const uint64_t
                  size_t ws_bytes_in, cudaStream_t s);
 int op_rotate(Context &c, const Keys &keys, const uint64_t *a, uint64_t g, uint64_t *out,
               uint32_t level, uint32_t count, void *ws, size_t ws_bytes_in, cudaStream_t s);
+int op_plain_import(Context &c, const int64_t *coeffs, uint32_t level, uint64_t *pt,
+                    cudaStream_t s);
+int op_mul_plain(Context &c, const uint64_t *a, const uint64_t *pt, uint64_t *out, uint32_t level,
+                 uint32_t count, cudaStream_t s);
+int op_rotate_hoisted(Context &c, const Keys &keys, const uint64_t *a, const uint64_t *gs,
+                      uint32_t n_rot, uint64_t *out, uint32_t level, uint32_t count, void *ws,
+                      size_t ws_bytes_in, cudaStream_t s);
 int op_rescale(Context &c, const uint64_t *a, uint64_t *out, uint32_t level, uint32_t count,
                void *ws, size_t ws_bytes_in, cudaStream_t s);
 int op_add(Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t level,
@@ -237,6 +244,27 @@ int catfhe_rotate(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
                   size_t ws_bytes, void *stream) {
     if (!keys_ok(ctx, keys) || !a || !out) return CATFHE_EINVAL;
     return op_rotate(ctx->c, *keys->k, a, galois_elt, out, level, count, ws, ws_bytes, S(stream));
+}
+
+int catfhe_plain_import(catfhe_ctx *ctx, const int64_t *coeffs, uint32_t level, uint64_t *pt,
+                        void *stream) {
+    if (!ctx || !coeffs || !pt) return CATFHE_EINVAL;
+    return op_plain_import(ctx->c, coeffs, level, pt, S(stream));
+}
+
+int catfhe_mul_plain(catfhe_ctx *ctx, const uint64_t *a, const uint64_t *pt, uint64_t *out,
+                     uint32_t level, uint32_t count, void *stream) {
+    if (!ctx || !a || !pt || !out) return CATFHE_EINVAL;
+    return op_mul_plain(ctx->c, a, pt, out, level, count, S(stream));
+}
+
+int catfhe_rotate_hoisted(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
+                          const uint64_t *galois_elts, uint32_t n_rot, uint64_t *out,
+                          uint32_t level, uint32_t count, void *ws, size_t ws_bytes,
+                          void *stream) {
+    if (!keys_ok(ctx, keys) || !a || (n_rot > 0 && !out)) return CATFHE_EINVAL;
+    return op_rotate_hoisted(ctx->c, *keys->k, a, galois_elts, n_rot, out, level, count, ws,
+                             ws_bytes, S(stream));
 }
 
 int catfhe_rescale(catfhe_ctx *ctx, const uint64_t *a, uint64_t *out, uint32_t level,

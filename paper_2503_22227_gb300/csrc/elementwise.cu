@@ -225,6 +225,50 @@ int launch_automorph_ntt(const Context &c, const uint64_t *in, uint64_t *out, ui
     return ok();
 }
 
+__global__ void __launch_bounds__(256)
+k_automorph_ntt_map(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, const LimbMap map,
+                    uint64_t g, uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t k = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t limb = blockIdx.y, grp = limb / map.period, r = limb % map.period;
+    const uint64_t *src = in + (size_t(grp) * map.src_stride + map.src_off[r]) * n;
+    uint64_t *dst = out + (size_t(grp) * map.dst_stride + map.dst_off[r]) * n;
+    const uint64_t mask2n = 2 * n - 1;
+    const uint32_t i = __brev(uint32_t(k)) >> (32 - log_n);
+    const uint64_t e = ((2 * uint64_t(i) + 1) * g) & mask2n;
+    dst[k] = src[__brev(uint32_t((e - 1) >> 1)) >> (32 - log_n)];
+}
+
+int launch_automorph_ntt_map(const Context &c, const uint64_t *in, uint64_t *out,
+                             const LimbMap &map, uint32_t limbs_total, uint64_t g, cudaStream_t s) {
+    if (limbs_total == 0) return CATFHE_OK;
+    k_automorph_ntt_map<<<coeff_grid(c.n, limbs_total), 256, 0, s>>>(in, out, map, g % (2 * c.n),
+                                                                      c.log_n);
+    return ok();
+}
+
+// ------------------------------------------------------------------ plaintext product
+
+__global__ void __launch_bounds__(256)
+k_mul_plain(const uint64_t *__restrict__ a, const uint64_t *__restrict__ pt, uint64_t *out,
+            uint32_t level, const DevMod *__restrict__ mods, uint32_t log_n) {
+    const size_t n = size_t(1) << log_n;
+    const size_t x = 2 * (size_t(blockIdx.x) * blockDim.x + threadIdx.x);
+    if (x >= n) return;
+    const uint32_t limb = blockIdx.y, i = limb % level;
+    const DevMod m = mods[i];
+    const ulonglong2 v = ld2(a + size_t(limb) * n + x), w = ld2(pt + size_t(i) * n + x);
+    st2(out + size_t(limb) * n + x, mul_mod(v.x, w.x, m), mul_mod(v.y, w.y, m));
+}
+
+int launch_mul_plain(const Context &c, const uint64_t *a, const uint64_t *pt, uint64_t *out,
+                     uint32_t level, uint32_t n_limbs, cudaStream_t s) {
+    if (n_limbs == 0) return CATFHE_OK;
+    k_mul_plain<<<coeff_grid(c.n / 2, n_limbs), 256, 0, s>>>(a, pt, out, level, c.d_mods, c.log_n);
+    return ok();
+}
+
 // Coefficient form: out[k] = +in[i] if i g = k (mod 2N), -in[i] if i g = k + N.
 __global__ void __launch_bounds__(256)
 k_automorph_coeff(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, const LimbMap map,

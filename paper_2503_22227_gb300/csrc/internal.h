@@ -237,6 +237,13 @@ int launch_combine(const Context &c, const CombineArgs &a, uint32_t count, cudaS
 
 int launch_automorph_ntt(const Context &c, const uint64_t *in, uint64_t *out, uint32_t limbs_total,
                          uint64_t g, cudaStream_t s);
+// NTT-form automorphism over the limbs a LimbMap selects (limbs_total =
+// groups x period); in and out must not overlap.
+int launch_automorph_ntt_map(const Context &c, const uint64_t *in, uint64_t *out,
+                             const LimbMap &map, uint32_t limbs_total, uint64_t g, cudaStream_t s);
+// out[ct][p][i] = a[ct][p][i] * pt[i] mod q_i (NTT form), n_limbs = count x 2 x level.
+int launch_mul_plain(const Context &c, const uint64_t *a, const uint64_t *pt, uint64_t *out,
+                     uint32_t level, uint32_t n_limbs, cudaStream_t s);
 int launch_automorph_coeff(const Context &c, const uint64_t *in, uint64_t *out,
                            const LimbMap &map, uint32_t n_limbs, uint64_t g, cudaStream_t s);
 int launch_add(const Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out,

@@ -328,6 +328,12 @@ size_t ws_bytes(const Context &c, int op, uint32_t level, uint32_t count) {
         case CATFHE_OP_MUL_RELIN_RESCALE:
             ks_layout(c, b, k, count, int(level), true);
             break;
+        case CATFHE_OP_ROTATE_HOISTED: {
+            ks_layout(c, b, k, count, int(level), false);
+            const int M = int(level) + c.K, beta = (int(level) + c.alpha - 1) / c.alpha;
+            b.take<uint64_t>(size_t(count) * beta * M * n);  // the shared lifted digits
+            break;
+        }
         case CATFHE_OP_RESCALE:
             b.take<uint64_t>(size_t(count) * 2 * n);
             b.take<uint64_t>(size_t(count) * 2 * (level ? level - 1 : 0) * n);
@@ -596,6 +602,71 @@ int op_rotate(Context &c, const Keys &keys, const uint64_t *a, uint64_t g, uint6
     return moddown(c, k.y, k.lift, out, addbuf, count, lvl, false, s);
 }
 
+// Hoisted rotations: one INTT + ModUp + NTT of a1, then per Galois element a
+// permutation of a0, a1 and the lifted digits, the inner product and ModDown.
+int op_rotate_hoisted(Context &c, const Keys &keys, const uint64_t *a, const uint64_t *gs,
+                      uint32_t n_rot, uint64_t *out, uint32_t level, uint32_t count, void *ws,
+                      size_t ws_bytes_in, cudaStream_t s) {
+    if (c.scheme == CATFHE_BFV) return CATFHE_ESCHEME;
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    if (n_rot > 0 && !gs) return CATFHE_EINVAL;
+    std::vector<const uint64_t *> gk(n_rot);
+    std::vector<uint64_t> gv(n_rot);
+    for (uint32_t r = 0; r < n_rot; r++) {
+        gv[r] = gs[r] % (2 * c.n);
+        if (!(gv[r] & 1)) return CATFHE_EINVAL;
+        TRY(key_for(keys, gv[r], &gk[r]));
+    }
+    if (count == 0 || n_rot == 0) return CATFHE_OK;
+    char *base;
+    TRY(get_ws(c, ws, ws_bytes_in, ws_bytes(c, CATFHE_OP_ROTATE_HOISTED, level, count), &base));
+    Bump bump{base};
+    KsBufs k{};
+    ks_layout(c, bump, k, count, int(level), false);
+    const size_t n = c.n;
+    const int lvl = int(level), M = lvl + c.K, beta = (lvl + c.alpha - 1) / c.alpha;
+    uint64_t *ext0 = bump.take<uint64_t>(size_t(count) * beta * M * n);
+    // a1 (NTT form) -> coefficient form -> lifted digits in NTT form, once
+    LimbMap m1{};
+    m1.period = uint32_t(lvl);
+    m1.src_stride = uint32_t(2 * lvl);
+    m1.dst_stride = uint32_t(lvl);
+    for (int i = 0; i < lvl; i++) {
+        m1.src_off[i] = uint16_t(lvl + i);
+        m1.dst_off[i] = uint16_t(i);
+        m1.prime[i] = uint8_t(i);
+    }
+    TRY(launch_ntt_inv(c, a, k.d2c, m1, uint32_t(lvl) * count, s));
+    TRY(modup(c, k.d2c, ext0, count, lvl, false, s));
+    TRY(ntt_ext(c, ext0, count, lvl, false, s));
+    // the lifted positions of ext (as ntt_ext selects them)
+    LimbMap me{};
+    uint32_t e = 0;
+    for (int j = 0; j < beta; j++) {
+        const int lo = j * c.alpha, hi = std::min((j + 1) * c.alpha, lvl);
+        for (int i = 0; i < M; i++) {
+            if (i >= lo && i < hi) continue;
+            if (e >= uint32_t(kMapMax)) return CATFHE_EINVAL;
+            me.src_off[e] = me.dst_off[e] = uint16_t(j * M + i);
+            me.prime[e] = uint8_t(ext_prime(c, lvl, i));
+            e++;
+        }
+    }
+    me.period = e;
+    me.src_stride = me.dst_stride = uint32_t(beta * M);
+    LimbMap m0 = m1;  // a0 -> d0
+    for (int i = 0; i < lvl; i++) m0.src_off[i] = uint16_t(i);
+    for (uint32_t r = 0; r < n_rot; r++) {
+        TRY(launch_automorph_ntt_map(c, a, k.d0, m0, uint32_t(lvl) * count, gv[r], s));
+        TRY(launch_automorph_ntt_map(c, a, k.d2, m1, uint32_t(lvl) * count, gv[r], s));
+        TRY(launch_automorph_ntt_map(c, ext0, k.ext, me, e * count, gv[r], s));
+        TRY(inner_product(c, k.ext, k.d2, gk[r], k.d0, nullptr, k.y, count, lvl, s));
+        TRY(moddown(c, k.y, k.lift, out + size_t(r) * count * 2 * lvl * n, nullptr, count, lvl,
+                    false, s));
+    }
+    return CATFHE_OK;
+}
+
 // CKKS rescale / BGV modulus switch: divide by q_{l-1}.
 int op_rescale(Context &c, const uint64_t *a, uint64_t *out, uint32_t level, uint32_t count,
                void *ws, size_t ws_bytes_in, cudaStream_t s) {
@@ -732,6 +803,40 @@ int op_add_const(Context &c, const uint64_t *a, int64_t k, uint64_t *out, uint32
         ks[i] = h_shoup(kv[i], q);
     }
     return launch_const_op(c, a, out, m, 2 * level * count, kv.data(), ks.data(), add.data(), s);
+}
+
+// Plaintext upload: the signed coefficients are staged in the last limb of
+// pt, converted to residues for the other limbs, then in place for the last
+// (each thread reads its own coefficient before writing it), then NTT.
+int op_plain_import(Context &c, const int64_t *coeffs, uint32_t level, uint64_t *pt,
+                    cudaStream_t s) {
+    if (c.scheme == CATFHE_BFV) return CATFHE_ESCHEME;
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    const size_t n = c.n;
+    int64_t *stage = reinterpret_cast<int64_t *>(pt + size_t(level - 1) * n);
+    if (cudaMemcpyAsync(stage, coeffs, n * 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return CATFHE_ECUDA;
+    if (level > 1) {
+        LimbMap m = map_identity(level - 1);
+        TRY(launch_small_to_rns(c, stage, pt, m, level - 1, nullptr, nullptr, 0, s));
+    }
+    LimbMap ml{};
+    ml.period = 1;
+    ml.src_stride = ml.dst_stride = 1;
+    ml.src_off[0] = ml.dst_off[0] = uint16_t(level - 1);
+    ml.prime[0] = uint8_t(level - 1);
+    TRY(launch_small_to_rns(c, stage, pt, ml, 1, nullptr, nullptr, 0, s));
+    LimbMap m = map_identity(level);
+    TRY(launch_ntt_fwd(c, pt, pt, m, level, s));
+    return cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
+}
+
+int op_mul_plain(Context &c, const uint64_t *a, const uint64_t *pt, uint64_t *out, uint32_t level,
+                 uint32_t count, cudaStream_t s) {
+    if (c.scheme == CATFHE_BFV) return CATFHE_ESCHEME;
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    if (count == 0) return CATFHE_OK;
+    return launch_mul_plain(c, a, pt, out, level, 2 * level * count, s);
 }
 
 // Keeps the first new_level limbs of each polynomial (dropping primes keeps

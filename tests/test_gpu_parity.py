@@ -418,3 +418,65 @@ def test_async_import_export_round_trip(ckks12):
     with pytest.raises(api.CatfheError) as e:
         pr.g.import_ct(host, api.FORM_NATIVE | 0x200)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("preset", [W.PRESETS["ckks_n12"], CKKS_DIGITS, SMALL_BGV],
+                         ids=lambda p: p.name)
+def test_hoisted_rotations_equal_single_rotations(preset):
+    """One shared ModUp for several Galois elements (rotations by 1, -3, 5
+    and the conjugation 2N-1): every output equals catfhe_rotate, and the
+    first equals the oracle's rotation."""
+    pr = Pair(preset)
+    gs = [pr.g.galois_elt(r) for r in (1, -3, 5)] + [2 * preset.n - 1]
+    for g in gs:
+        pr.gk.gen_galois(g)
+        pr.ok.gen_galois(g)
+    for level in sorted({preset.L, max(1, preset.L - 2)}):
+        a, _ = _uniform_pair(pr, level, 3, f"hoist-{preset.name}-{level}")
+        da = pr.g.import_ct(a)
+        out = pr.g.rotate_hoisted(pr.gk, da, gs)
+        assert tuple(out.shape) == (len(gs), 3, 2, level, preset.n)
+        for r, g in enumerate(gs):
+            assert torch.equal(out[r], pr.g.rotate(pr.gk, da, g)), (level, g)
+        got = pr.g.export_ct(out[0])
+        assert np.array_equal(got[1], pr.o.rotate(pr.ok, a[1], gs[0]))
+
+
+def test_hoisted_rotation_errors(ckks12):
+    pr = ckks12
+    a, _ = _uniform_pair(pr, 3, 1, "hoist-err")
+    da = pr.g.import_ct(a)
+    with pytest.raises(api.CatfheError) as e:      # no key for 7 steps, nothing enqueued
+        pr.g.rotate_hoisted(pr.gk, da, [pr.g.galois_elt(1), pr.g.galois_elt(7)])
+    assert e.value.code == -3
+    with pytest.raises(api.CatfheError) as e:
+        pr.g.rotate_hoisted(pr.gk, da, [4])
+    assert e.value.code == -1
+    empty = pr.g.rotate_hoisted(pr.gk, da, [])
+    assert empty.shape[0] == 0
+    bfv = Pair(SMALL_BFV)
+    b, _ = _uniform_pair(bfv, SMALL_BFV.L, 1, "hoist-bfv")
+    with pytest.raises(api.CatfheError) as e:
+        bfv.g.rotate_hoisted(bfv.gk, bfv.g.import_ct(b), [bfv.g.galois_elt(1)])
+    assert e.value.code == -6
+
+
+@pytest.mark.parametrize("preset", [W.PRESETS["ckks_n12"], SMALL_BGV], ids=lambda p: p.name)
+def test_mul_plain_matches_oracle(preset):
+    pr = Pair(preset)
+    rng = np.random.default_rng(41)
+    pt = rng.integers(-2 ** 40, 2 ** 40, preset.n)
+    for level in sorted({preset.L, max(1, preset.L - 1)}):
+        a, _ = _uniform_pair(pr, level, 2, f"mulplain-{preset.name}-{level}")
+        da = pr.g.import_ct(a)
+        dpt = pr.g.plain_import(pt, level)
+        got = pr.g.export_ct(pr.g.mul_plain(da, dpt))
+        for c in range(2):
+            assert np.array_equal(got[c], pr.o.mul_plain(a[c], pt)), (level, c)
+        out = pr.g.empty_ct(2, level)
+        api.run_batch([api.make_op(api.OP_MUL_PLAIN, pr.g, da, out, b=dpt)], lanes=1)
+        assert np.array_equal(pr.g.export_ct(out), got)
+    bfv = Pair(SMALL_BFV)
+    with pytest.raises(api.CatfheError) as e:
+        bfv.g.plain_import(pt, SMALL_BFV.L)
+    assert e.value.code == -6

@@ -274,3 +274,27 @@ def test_elementwise_ops_by_decryption(bgv_small, ckks_n12):
     want[0] += -(2 ** 35)
     assert np.array_equal(ctx.decrypt(keys, ctx.add_const(ca, -(2 ** 35))), want)
     assert np.array_equal(ctx.decrypt(keys, ctx.drop(ca, 1)), da)
+
+
+def test_mul_plain_by_decryption(bgv_small, ckks_n12):
+    """Multiplication by a plaintext polynomial: decryption is linear, so
+    Dec(c pt) = Dec(c) pt in Z[X]/(X^N + 1) (mod t for BGV; exactly, as
+    integers, for small CKKS messages)."""
+    ctx, keys = bgv_small
+    n, t = ctx.n, ctx.t
+    rng = np.random.default_rng(31)
+    m = W.int_messages(rng, n, t)
+    pt = rng.integers(-3, 4, n)
+    c = ctx.encrypt(keys, m, W.seed_for("mp-bgv"))
+    want = negamul_int([int(x) for x in m], [int(x) for x in pt], t)
+    assert [int(x) for x in ctx.decrypt(keys, ctx.mul_plain(c, pt))] == want
+
+    ctx, keys = ckks_n12
+    n = ctx.n
+    rng = np.random.default_rng(32)
+    m = rng.integers(-2 ** 20, 2 ** 20, n)
+    pt = rng.integers(-2 ** 10, 2 ** 10, n)
+    c = ctx.encrypt(keys, m, W.seed_for("mp-ckks"))
+    d = ctx.decrypt(keys, c)
+    want = negamul_int([int(x) for x in d], [int(x) for x in pt])
+    assert [int(x) for x in ctx.decrypt(keys, ctx.mul_plain(c, pt))] == want
