@@ -11,7 +11,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -22,9 +24,10 @@ namespace catfhe {
 size_t ws_bytes(const Context &c, int op, uint32_t level, uint32_t count);
 int op_mul_relin(Context &c, const Keys &keys, const uint64_t *a, const uint64_t *b,
                  uint64_t *out, uint32_t level, uint32_t count, bool fused, void *ws,
-                 size_t ws_bytes_in, cudaStream_t s);
+                 size_t ws_bytes_in, cudaStream_t s, const Gather *gth);
 int op_rotate(Context &c, const Keys &keys, const uint64_t *a, uint64_t g, uint64_t *out,
-              uint32_t level, uint32_t count, void *ws, size_t ws_bytes_in, cudaStream_t s);
+              uint32_t level, uint32_t count, void *ws, size_t ws_bytes_in, cudaStream_t s,
+              const Gather *gth);
 int op_rescale(Context &c, const uint64_t *a, uint64_t *out, uint32_t level, uint32_t count,
                void *ws, size_t ws_bytes_in, cudaStream_t s);
 int op_add(Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t level,
@@ -138,37 +141,93 @@ double op_cost(const catfhe_op &o) {
     return o.count * (ntt * n / 2 * lg + prod * n);
 }
 
+// A unit of work on one lane: one entry, or several single-ciphertext
+// entries of the same kind, context, keys, level (and Galois element) merged
+// into one gathered operation.
+struct Unit {
+    std::vector<uint32_t> entries;
+};
+
 struct Plan {
-    std::vector<std::vector<uint32_t>> lane_ops;
+    std::vector<Unit> units;
+    std::vector<std::vector<uint32_t>> lane_units;
     std::vector<size_t> lane_ws;  // bytes, 256-aligned
     size_t total = 0;
 };
 
+bool mergeable(const catfhe_op &o) {
+    return o.count == 1 && o.ctx->c.scheme != CATFHE_BFV &&
+           (o.op == CATFHE_OP_MUL_RELIN || o.op == CATFHE_OP_MUL_RELIN_RESCALE ||
+            o.op == CATFHE_OP_ROTATE);
+}
+
+// Merging: compatible entries are split into ceil(group / lanes) sized
+// gathers (at most kGatherMax), so a large group still spreads over every
+// lane while each launch sequence covers several ciphertexts.
+void make_units(const catfhe_op *ops, uint32_t n, uint32_t lanes, std::vector<Unit> &units) {
+    std::map<std::tuple<int, const void *, const void *, uint32_t, uint64_t>, std::vector<uint32_t>>
+        groups;
+    std::vector<uint32_t> order;  // first entry of each group, in submission order
+    for (uint32_t i = 0; i < n; i++) {
+        const catfhe_op &o = ops[i];
+        if (!mergeable(o)) {
+            units.push_back(Unit{{i}});
+            continue;
+        }
+        const uint64_t g = o.op == CATFHE_OP_ROTATE ? o.arg % (2 * o.ctx->c.n) : 0;
+        auto &v = groups[std::make_tuple(o.op, (const void *)o.ctx, (const void *)o.keys, o.level, g)];
+        if (v.empty()) order.push_back(i);
+        v.push_back(i);
+    }
+    for (uint32_t first : order) {
+        const catfhe_op &o = ops[first];
+        const uint64_t g = o.op == CATFHE_OP_ROTATE ? o.arg % (2 * o.ctx->c.n) : 0;
+        const auto &v = groups[std::make_tuple(o.op, (const void *)o.ctx, (const void *)o.keys, o.level, g)];
+        const size_t per = std::min<size_t>(kGatherMax, (v.size() + lanes - 1) / lanes);
+        for (size_t k = 0; k < v.size(); k += per) {
+            Unit u;
+            u.entries.assign(v.begin() + k, v.begin() + std::min(v.size(), k + per));
+            units.push_back(std::move(u));
+        }
+    }
+}
+
 int plan_batch(const catfhe_op *ops, uint32_t n, uint32_t lanes, Plan &p) {
     if (!ops || n == 0) return CATFHE_EINVAL;
     lanes = std::max<uint32_t>(1, std::min<uint32_t>(std::min<uint32_t>(lanes, n), kMaxLanes));
-    std::vector<uint32_t> order(n);
     for (uint32_t i = 0; i < n; i++) {
         const int rc = check_op(ops[i]);
         if (rc) return rc;
-        order[i] = i;
     }
-    std::vector<double> cost(n);
-    for (uint32_t i = 0; i < n; i++) cost[i] = op_cost(ops[i]);
+    p.units.clear();
+    make_units(ops, n, lanes, p.units);
+    const uint32_t nu = uint32_t(p.units.size());
+    std::vector<uint32_t> order(nu);
+    std::vector<double> cost(nu, 0.0);
+    for (uint32_t u = 0; u < nu; u++) {
+        order[u] = u;
+        for (uint32_t i : p.units[u].entries) cost[u] += op_cost(ops[i]);
+    }
     std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return cost[x] > cost[y]; });
-    p.lane_ops.assign(lanes, {});
-    p.lane_ws.assign(lanes, 0);
-    std::vector<double> load(lanes, 0.0);
-    for (uint32_t i : order) {
+    const uint32_t nl = std::min(lanes, nu);
+    p.lane_units.assign(nl, {});
+    p.lane_ws.assign(nl, 0);
+    std::vector<double> load(nl, 0.0);
+    for (uint32_t u : order) {
         const uint32_t l = uint32_t(std::min_element(load.begin(), load.end()) - load.begin());
-        load[l] += cost[i];
-        p.lane_ops[l].push_back(i);
-        const catfhe_op &o = ops[i];
-        const size_t w = needs_ws(o.op) ? ws_bytes(o.ctx->c, o.op, o.level, o.count) : 0;
+        load[l] += cost[u];
+        p.lane_units[l].push_back(u);
+        const catfhe_op &o = ops[p.units[u].entries[0]];
+        const uint32_t items = p.units[u].entries.size() > 1 ? uint32_t(p.units[u].entries.size())
+                                                             : o.count;
+        const size_t w = needs_ws(o.op) ? ws_bytes(o.ctx->c, o.op, o.level, items) : 0;
         p.lane_ws[l] = std::max(p.lane_ws[l], (w + 255) & ~size_t(255));
     }
     // within a lane, run in submission order
-    for (auto &v : p.lane_ops) std::sort(v.begin(), v.end());
+    for (auto &v : p.lane_units)
+        std::sort(v.begin(), v.end(), [&](uint32_t x, uint32_t y) {
+            return p.units[x].entries[0] < p.units[y].entries[0];
+        });
     p.total = 0;
     for (size_t w : p.lane_ws) p.total += w;
     return CATFHE_OK;
@@ -178,11 +237,11 @@ int run_one(const catfhe_op &o, void *ws, size_t ws_bytes_in, cudaStream_t s) {
     Context &c = o.ctx->c;
     switch (o.op) {
         case CATFHE_OP_MUL_RELIN:
-            return op_mul_relin(c, *o.keys->k, o.a, o.b, o.out, o.level, o.count, false, ws, ws_bytes_in, s);
+            return op_mul_relin(c, *o.keys->k, o.a, o.b, o.out, o.level, o.count, false, ws, ws_bytes_in, s, nullptr);
         case CATFHE_OP_MUL_RELIN_RESCALE:
-            return op_mul_relin(c, *o.keys->k, o.a, o.b, o.out, o.level, o.count, true, ws, ws_bytes_in, s);
+            return op_mul_relin(c, *o.keys->k, o.a, o.b, o.out, o.level, o.count, true, ws, ws_bytes_in, s, nullptr);
         case CATFHE_OP_ROTATE:
-            return op_rotate(c, *o.keys->k, o.a, o.arg, o.out, o.level, o.count, ws, ws_bytes_in, s);
+            return op_rotate(c, *o.keys->k, o.a, o.arg, o.out, o.level, o.count, ws, ws_bytes_in, s, nullptr);
         case CATFHE_OP_RESCALE:
             return op_rescale(c, o.a, o.out, o.level, o.count, ws, ws_bytes_in, s);
         case CATFHE_OP_ADD:
@@ -202,20 +261,42 @@ int run_one(const catfhe_op &o, void *ws, size_t ws_bytes_in, cudaStream_t s) {
     }
 }
 
+int run_unit(const catfhe_op *ops, const Unit &u, void *ws, size_t ws_bytes_in, cudaStream_t s) {
+    const catfhe_op &o = ops[u.entries[0]];
+    if (u.entries.size() == 1) return o.count ? run_one(o, ws, ws_bytes_in, s) : CATFHE_OK;
+    Gather g;
+    g.n = uint32_t(u.entries.size());
+    for (uint32_t k = 0; k < g.n; k++) {
+        const catfhe_op &e = ops[u.entries[k]];
+        g.a[k] = e.a;
+        g.b[k] = e.b;
+        g.out[k] = e.out;
+    }
+    Context &c = o.ctx->c;
+    switch (o.op) {
+        case CATFHE_OP_MUL_RELIN:
+        case CATFHE_OP_MUL_RELIN_RESCALE:
+            return op_mul_relin(c, *o.keys->k, o.a, o.b, o.out, o.level, g.n,
+                                o.op == CATFHE_OP_MUL_RELIN_RESCALE, ws, ws_bytes_in, s, &g);
+        case CATFHE_OP_ROTATE:
+            return op_rotate(c, *o.keys->k, o.a, o.arg, o.out, o.level, g.n, ws, ws_bytes_in, s, &g);
+        default:
+            return CATFHE_EINVAL;
+    }
+}
+
 int run_plan(const catfhe_op *ops, const Plan &p, char *ws, cudaStream_t s) {
     LanePool *pool;
     int rc = lane_pool(&pool);
     if (rc) return rc;
-    const size_t lanes = p.lane_ops.size();
+    const size_t lanes = p.lane_units.size();
     if (cudaEventRecord(pool->start, s) != cudaSuccess) return CATFHE_ECUDA;
     size_t off = 0;
     for (size_t l = 0; l < lanes; l++) {
         cudaStream_t ls = pool->s[l];
         if (cudaStreamWaitEvent(ls, pool->start, 0) != cudaSuccess) return CATFHE_ECUDA;
-        for (uint32_t i : p.lane_ops[l]) {
-            const catfhe_op &o = ops[i];
-            if (o.count == 0) continue;
-            rc = run_one(o, ws + off, p.lane_ws[l], ls);
+        for (uint32_t u : p.lane_units[l]) {
+            rc = run_unit(ops, p.units[u], ws + off, p.lane_ws[l], ls);
             if (rc) return rc;
         }
         off += p.lane_ws[l];

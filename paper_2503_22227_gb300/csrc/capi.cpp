@@ -12,9 +12,11 @@ void ctx_free(Context &c);
 size_t ws_bytes(const Context &c, int op, uint32_t level, uint32_t count);
 int op_mul_relin(Context &c, const Keys &keys, const uint64_t *a, const uint64_t *b,
                  uint64_t *out, uint32_t level, uint32_t count, bool fused, void *ws,
-                 size_t ws_bytes_in, cudaStream_t s);
+                 size_t ws_bytes_in, cudaStream_t s,
+                 const Gather *gth = nullptr);
 int op_rotate(Context &c, const Keys &keys, const uint64_t *a, uint64_t g, uint64_t *out,
-              uint32_t level, uint32_t count, void *ws, size_t ws_bytes_in, cudaStream_t s);
+              uint32_t level, uint32_t count, void *ws, size_t ws_bytes_in, cudaStream_t s,
+              const Gather *gth = nullptr);
 int op_plain_import(Context &c, const int64_t *coeffs, uint32_t level, uint64_t *pt,
                     cudaStream_t s);
 int op_mul_plain(Context &c, const uint64_t *a, const uint64_t *pt, uint64_t *out, uint32_t level,

@@ -36,7 +36,8 @@ k_tensor(const TensorArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
     const uint32_t i = blockIdx.y, item = blockIdx.z;
     if (x >= n) return;
     const DevMod m = mods[A.prime[i]];
-    const uint64_t *a = A.a + item * A.in_item, *b = A.b + item * A.in_item;
+    const uint64_t *a = A.gathered ? A.ga[item] : A.a + item * A.in_item;
+    const uint64_t *b = A.gathered ? A.gb[item] : A.b + item * A.in_item;
     const size_t l0 = size_t(i) * n + x, l1 = (size_t(A.limbs) + i) * n + x;
     const ulonglong2 a0 = ld2(a + l0), a1 = ld2(a + l1), b0 = ld2(b + l0), b1 = ld2(b + l1);
     const size_t o = item * A.out_item + size_t(i) * n + x;

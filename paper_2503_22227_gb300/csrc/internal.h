@@ -15,6 +15,8 @@ namespace catfhe {
 
 constexpr int kMaxPrimes = 128;   // global prime table (q, p, b)
 constexpr int kMapMax = 128;      // limbs per group in one LimbMap
+// Largest number of separately addressed ciphertexts in one operation (Gather).
+constexpr int kGatherMax = 8;
 constexpr int kConvMaxK = 32;     // sources of one exact base conversion
 constexpr int kConvMaxT = 48;     // targets of one exact base conversion
 
@@ -174,6 +176,8 @@ struct NttEpilogue {
     uint32_t y_stride, add_stride, out_stride;  // per group, in limbs
     uint16_t y_off[kMapMax], add_off[kMapMax], out_off[kMapMax];
     uint64_t dinv[kMapMax], dinv_s[kMapMax];
+    uint32_t gathered;                          // nonzero: group g writes gout[g]
+    uint64_t *gout[kGatherMax];
 };
 int launch_ntt_fwd_combine(const Context &c, uint64_t *lift, const LimbMap &map, uint32_t n_limbs,
                            const NttEpilogue &epi, cudaStream_t s);
@@ -199,12 +203,27 @@ int launch_bfv_scale_round(const Context &c, const uint64_t *q_to_b, uint32_t q_
                            cudaStream_t s);
 
 // Element-wise kernels (elementwise.cu)
+// Per-ciphertext base pointers of an operation whose ciphertexts are not
+// contiguous: an uneven batch merges compatible single-ciphertext entries
+// into one operation of count = n items; item i reads a[i] (and b[i]) and
+// writes out[i], each u64[2][level][N].  Only the kernels that touch the
+// caller's buffers (the tensor's loads, the automorphism's loads, ModDown's
+// final stores) look at it; everything between runs on contiguous workspace.
+struct Gather {
+    uint32_t n = 0;
+    const uint64_t *a[kGatherMax];
+    const uint64_t *b[kGatherMax];
+    uint64_t *out[kGatherMax];
+};
+
 struct TensorArgs {
     const uint64_t *a, *b;       // [count][2][limbs][N]
     uint64_t *d0, *d1, *d2;      // each [count][limbs][N] (item stride given)
     size_t in_item, out_item;    // item strides in elements
     uint32_t limbs;
     uint8_t prime[kMapMax];
+    uint32_t gathered;           // nonzero: item i reads ga[i], gb[i]
+    const uint64_t *ga[kGatherMax], *gb[kGatherMax];
 };
 int launch_tensor(const Context &c, const TensorArgs &a, uint32_t count, cudaStream_t s);
 

@@ -248,7 +248,8 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
         // ModDown combine: out = (y - lift) * D^-1 (+ add), lift now in NTT form
         const size_t off = size_t(h) * R;
         const uint64_t *yp = epi.y + (size_t(g) * epi.y_stride + epi.y_off[r]) * N + off;
-        uint64_t *op = epi.out + (size_t(g) * epi.out_stride + epi.out_off[r]) * N + off;
+        uint64_t *op = (epi.gathered ? epi.gout[g] : epi.out + size_t(g) * epi.out_stride * N) +
+                       size_t(epi.out_off[r]) * N + off;
         const uint64_t *ap =
             epi.add ? epi.add + (size_t(g) * epi.add_stride + epi.add_off[r]) * N + off : nullptr;
         const uint64_t dv = epi.dinv[r], dvs = epi.dinv_s[r];

@@ -193,7 +193,8 @@ static int inner_product(Context &c, const uint64_t *ext, const uint64_t *own, c
 // ModDown of y ([count][2][M][N]; NTT form for CKKS/BGV, coefficient form
 // for BFV) by D = P (fused: P q_{l-1}) into out ([count][2][lo][N]).
 static int moddown(Context &c, uint64_t *y, uint64_t *lift, uint64_t *out, const uint64_t *add,
-                   uint32_t count, int level, bool fused, cudaStream_t s) {
+                   uint32_t count, int level, bool fused, cudaStream_t s,
+                   const Gather *gth = nullptr) {
     const int M = level + c.K, lo = fused ? level - 1 : level;
     const size_t n = c.n;
     const bool ntt_form = c.scheme != CATFHE_BFV;
@@ -239,10 +240,15 @@ static int moddown(Context &c, uint64_t *y, uint64_t *lift, uint64_t *out, const
         dinv[i] = h_invmod(D, q);
         dinv_s[i] = h_shoup(dinv[i], q);
     }
+    if (gth && gth->n && (!ntt_form || add || gth->n != count)) return CATFHE_EINVAL;
     if (ntt_form) {
         // NTT of the lift whose last pass writes (y - lift) D^-1 straight to out
         LimbMap m{};
         NttEpilogue e{};
+        if (gth && gth->n) {
+            e.gathered = 1;
+            for (uint32_t i = 0; i < gth->n; i++) e.gout[i] = gth->out[i];
+        }
         m.period = uint32_t(2 * lo);
         m.src_stride = m.dst_stride = uint32_t(2 * lo);
         e.y = y;
@@ -365,13 +371,20 @@ static int key_for(const Keys &k, uint64_t id, const uint64_t **key) {
 // P*(d0, d1) folded in, ModDown (fused: by P q_{l-1}).
 static int mul_relin_ntt(Context &c, const Keys &keys, const uint64_t *a, const uint64_t *b,
                          uint64_t *out, uint32_t count, int level, bool fused, KsBufs &k,
-                         cudaStream_t s) {
+                         cudaStream_t s, const Gather *gth) {
     const uint64_t *rlk;
     TRY(key_for(keys, 0, &rlk));
     const size_t n = c.n;
     TensorArgs t{};
     t.a = a;
     t.b = b;
+    if (gth && gth->n) {
+        t.gathered = 1;
+        for (uint32_t i = 0; i < gth->n; i++) {
+            t.ga[i] = gth->a[i];
+            t.gb[i] = gth->b[i];
+        }
+    }
     t.d0 = k.d0;
     t.d1 = k.d1;
     t.d2 = k.d2;
@@ -385,7 +398,7 @@ static int mul_relin_ntt(Context &c, const Keys &keys, const uint64_t *a, const 
     TRY(modup(c, k.d2c, k.ext, count, level, false, s));
     TRY(ntt_ext(c, k.ext, count, level, false, s));
     TRY(inner_product(c, k.ext, k.d2, rlk, k.d0, k.d1, k.y, count, level, s));
-    return moddown(c, k.y, k.lift, out, nullptr, count, level, fused, s);
+    return moddown(c, k.y, k.lift, out, nullptr, count, level, fused, s, gth);
 }
 
 // BFV: lift to Q u B, NTT, tensor, INTT, exact round(t x / Q) back to Q,
@@ -522,7 +535,9 @@ static int mul_relin_bfv(Context &c, const Keys &keys, const uint64_t *a, const 
 
 int op_mul_relin(Context &c, const Keys &keys, const uint64_t *a, const uint64_t *b,
                  uint64_t *out, uint32_t level, uint32_t count, bool fused, void *ws,
-                 size_t ws_bytes_in, cudaStream_t s) {
+                 size_t ws_bytes_in, cudaStream_t s, const Gather *gth) {
+    if (gth && gth->n && (c.scheme == CATFHE_BFV || gth->n != count || count > kGatherMax))
+        return CATFHE_EINVAL;
     if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
     if (fused && (c.scheme != CATFHE_CKKS)) return CATFHE_ESCHEME;
     if (fused && level < 2) return CATFHE_ELEVEL;
@@ -535,12 +550,15 @@ int op_mul_relin(Context &c, const Keys &keys, const uint64_t *a, const uint64_t
     KsBufs k{};
     ks_layout(c, bump, k, count, int(level), fused);
     if (c.scheme == CATFHE_BFV) return mul_relin_bfv(c, keys, a, b, out, count, int(level), k, s);
-    return mul_relin_ntt(c, keys, a, b, out, count, int(level), fused, k, s);
+    return mul_relin_ntt(c, keys, a, b, out, count, int(level), fused, k, s, gth);
 }
 
 int op_rotate(Context &c, const Keys &keys, const uint64_t *a, uint64_t g, uint64_t *out,
-              uint32_t level, uint32_t count, void *ws, size_t ws_bytes_in, cudaStream_t s) {
+              uint32_t level, uint32_t count, void *ws, size_t ws_bytes_in, cudaStream_t s,
+              const Gather *gth) {
     if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    if (gth && gth->n && (c.scheme == CATFHE_BFV || gth->n != count || count > kGatherMax))
+        return CATFHE_EINVAL;
     g %= 2 * c.n;
     if (!(g & 1)) return CATFHE_EINVAL;
     const uint64_t *gk;
@@ -556,7 +574,7 @@ int op_rotate(Context &c, const Keys &keys, const uint64_t *a, uint64_t g, uint6
     if (c.scheme != CATFHE_BFV) {
         // sigma_g on both components in NTT form: d0 <- sigma(c0), d2 <- sigma(c1)
         for (uint32_t ct = 0; ct < count; ct++) {
-            const uint64_t *src = a + size_t(ct) * 2 * lvl * n;
+            const uint64_t *src = (gth && gth->n) ? gth->a[ct] : a + size_t(ct) * 2 * lvl * n;
             TRY(launch_automorph_ntt(c, src, k.d0 + size_t(ct) * lvl * n, uint32_t(lvl), g, s));
             TRY(launch_automorph_ntt(c, src + size_t(lvl) * n, k.d2 + size_t(ct) * lvl * n,
                                      uint32_t(lvl), g, s));
@@ -566,7 +584,7 @@ int op_rotate(Context &c, const Keys &keys, const uint64_t *a, uint64_t g, uint6
         TRY(modup(c, k.d2c, k.ext, count, lvl, false, s));
         TRY(ntt_ext(c, k.ext, count, lvl, false, s));
         TRY(inner_product(c, k.ext, k.d2, gk, k.d0, nullptr, k.y, count, lvl, s));
-        return moddown(c, k.y, k.lift, out, nullptr, count, lvl, false, s);
+        return moddown(c, k.y, k.lift, out, nullptr, count, lvl, false, s, gth);
     }
     // BFV (coefficient form): (sigma(c0), 0) becomes the added pair of the
     // ModDown combine, sigma(c1) is key switched.

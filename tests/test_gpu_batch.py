@@ -108,3 +108,52 @@ def test_batch_rejects_bad_entries():
         api.run_batch([api.make_op(api.OP_ROTATE, ctx, a3, out3, keys=keys,
                                    galois_elt=ctx.galois_elt(9))], lanes=1)
     assert e.value.code in (-1, -3)   # missing Galois key
+
+
+def test_compatible_entries_are_merged_and_exact():
+    """Single-ciphertext HMult+relin(+rescale) and HRotate entries of the same
+    context, keys, level (and Galois element) are gathered into one batched
+    operation by the batch planner; every output must equal the single call,
+    eager and from a captured graph, whatever the lane count."""
+    ctx, keys, gs = _ctx(W.PRESETS["ckks_n12"], (1, 3))
+    ctx2, keys2, gs2 = _ctx(W.Preset("ckks_n13", W.CKKS, 13, (45,) * 6, (50, 50), 3, log_n_max=13),
+                            (1,))
+    seed = W.seed_for("merge-in")
+    jobs = []
+    for j in range(11):
+        jobs.append((api.OP_MUL_RELIN_RESCALE, ctx, keys, 3, gs[0]))
+    for j in range(5):
+        jobs.append((api.OP_MUL_RELIN, ctx, keys, 2, gs[0]))
+    for j in range(7):
+        jobs.append((api.OP_ROTATE, ctx, keys, 3, gs[j % 2]))
+    for j in range(6):
+        jobs.append((api.OP_MUL_RELIN_RESCALE, ctx2, keys2, 4, gs2[0]))
+    ops, outs, wants, keep = [], [], [], []
+    for j, (kind, c, k, level, g) in enumerate(jobs):
+        a = c.ct_uniform(seed, 2 * j, level)
+        b = c.ct_uniform(seed, 2 * j + 1, level)
+        if kind == api.OP_MUL_RELIN:
+            want = c.mul_relin(k, a, b)
+        elif kind == api.OP_MUL_RELIN_RESCALE:
+            want = c.mul_relin_rescale(k, a, b)
+        else:
+            want = c.rotate(k, a, g)
+        out = torch.full_like(want, -1)
+        ops.append(api.make_op(kind, c, a, out, keys=k, b=b, galois_elt=g))
+        outs.append(out)
+        wants.append(want.clone())
+        keep.append((a, b))
+    for lanes in (1, 2, 5):
+        for o in outs:
+            o.fill_(-1)
+        api.run_batch(ops, lanes=lanes)
+        torch.cuda.synchronize()
+        for j, (o, w) in enumerate(zip(outs, wants)):
+            assert torch.equal(o, w), (lanes, j)
+    graph = api.Graph(ops, lanes=3)
+    for o in outs:
+        o.fill_(-1)
+    graph.launch()
+    torch.cuda.synchronize()
+    for j, (o, w) in enumerate(zip(outs, wants)):
+        assert torch.equal(o, w), ("graph", j)
