@@ -79,7 +79,10 @@ enum {
     /* workspace of catfhe_rotate_hoisted (any number of rotations) */
     CATFHE_OP_ROTATE_HOISTED = 13,
     /* batch entry: out = a * plaintext b (catfhe_mul_plain; no workspace) */
-    CATFHE_OP_MUL_PLAIN = 14
+    CATFHE_OP_MUL_PLAIN = 14,
+    /* workspaces of catfhe_encode_ckks / catfhe_decode_ckks */
+    CATFHE_OP_ENCODE = 15,
+    CATFHE_OP_DECODE = 16
 };
 
 /* Forms for catfhe_ct_import / catfhe_ct_export. */
@@ -233,6 +236,26 @@ int catfhe_add_const(catfhe_ctx *ctx, const uint64_t *a, int64_t k, uint64_t *ou
  * the host copy. */
 int catfhe_plain_import(catfhe_ctx *ctx, const int64_t *coeffs, uint32_t level, uint64_t *pt,
                         void *stream);
+
+/* CKKS encoding on the device (Table 1 "encode"): host slots z, N/2
+ * complex numbers as interleaved (re, im) doubles, become the plaintext
+ * m with m(zeta^(5^k)) ~ scale z_k (zeta = exp(i pi / N), conjugate slots
+ * implied): one length-N DFT of float64, coefficients rounded half away
+ * from zero (|m_i| must stay below 2^62), reduced mod q_0 .. q_{level-1}
+ * and NTT'd into pt u64[level][N] (a plaintext for catfhe_mul_plain).
+ * ESCHEME unless CKKS.  Workspace: catfhe_workspace_bytes(CATFHE_OP_ENCODE,
+ * level, 1) or NULL.  Synchronises. */
+int catfhe_encode_ckks(catfhe_ctx *ctx, const double *slots, double scale, uint32_t level,
+                       uint64_t *pt, void *ws, size_t ws_bytes, void *stream);
+
+/* CKKS decryption and decoding on the device (Table 1 "decrypt",
+ * "decode"): the centred plaintext of ct (as catfhe_decrypt, exact while
+ * below 2^63 in magnitude), evaluated at the slot roots by one float64 DFT
+ * and divided by scale, into host slots (N/2 interleaved complex doubles).
+ * ESCHEME unless CKKS.  Workspace: CATFHE_OP_DECODE.  Synchronises. */
+int catfhe_decode_ckks(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *ct,
+                       uint32_t level, double scale, double *slots, void *ws, size_t ws_bytes,
+                       void *stream);
 
 /* Multiplication by a plaintext (Table 1 "multiply_plain"): both
  * polynomials times pt, limb by limb in NTT form; pt u64[>= level][N] from

@@ -24,6 +24,7 @@ OP_MUL_RELIN, OP_MUL_RELIN_RESCALE, OP_ROTATE, OP_RESCALE, OP_DECRYPT, OP_EXPORT
 OP_ADD, OP_SUB, OP_MUL_INT, OP_ADD_CONST, OP_DROP = range(8, 13)
 OP_ROTATE_HOISTED = 13
 OP_MUL_PLAIN = 14
+OP_ENCODE, OP_DECODE = 15, 16
 FORM_COEFF, FORM_NATIVE = 0, 1
 FORM_ASYNC = 0x100      # OR-ed into a form: import / export without synchronising
 
@@ -40,6 +41,7 @@ EXPORTS = [
     "catfhe_tune_ntt", "catfhe_ntt_schedule", "catfhe_set_ntt_schedule",
     "catfhe_sub", "catfhe_mul_int", "catfhe_add_const", "catfhe_drop_level",
     "catfhe_rotate_hoisted", "catfhe_plain_import", "catfhe_mul_plain",
+    "catfhe_encode_ckks", "catfhe_decode_ckks",
 ]
 
 
@@ -107,6 +109,8 @@ def load(path: str = LIB_PATH):
             "catfhe_rotate_hoisted": (ctypes.c_int, [vp, vp, vp, vp, u32, vp, u32, u32, vp, sz, vp]),
             "catfhe_plain_import": (ctypes.c_int, [vp, vp, u32, vp, vp]),
             "catfhe_mul_plain": (ctypes.c_int, [vp, vp, vp, vp, u32, u32, vp]),
+            "catfhe_encode_ckks": (ctypes.c_int, [vp, vp, ctypes.c_double, u32, vp, vp, sz, vp]),
+            "catfhe_decode_ckks": (ctypes.c_int, [vp, vp, vp, u32, ctypes.c_double, vp, vp, sz, vp]),
             "catfhe_rescale": (ctypes.c_int, [vp, vp, vp, u32, u32, vp, sz, vp]),
             "catfhe_decrypt": (ctypes.c_int, [vp, vp, vp, u32, u64, vp, vp, sz, vp]),
             "catfhe_ntt": (ctypes.c_int, [vp, vp, u32, u32, ctypes.c_int, vp]),
@@ -365,6 +369,30 @@ class Context:
         _check(load().catfhe_plain_import(self._h, m.ctypes.data_as(vp), level, _ptr(pt), _stream()),
                "catfhe_plain_import")
         return pt
+
+    def encode_ckks(self, slots, scale: float, level: int | None = None):
+        """N/2 complex slots -> device plaintext [level][N] (NTT form), encoded
+        on the device."""
+        level = self.L if level is None else level
+        z = np.ascontiguousarray(np.asarray(slots, dtype=np.complex128))
+        assert z.shape == (self.n // 2,)
+        torch = _torch()
+        pt = torch.empty((level, self.n), dtype=torch.int64, device="cuda")
+        ws = self.workspace(OP_ENCODE, level, 1)
+        _check(load().catfhe_encode_ckks(self._h, z.ctypes.data_as(vp), float(scale), level,
+                                         _ptr(pt), _ptr(ws), ws.numel(), _stream()),
+               "catfhe_encode_ckks")
+        return pt
+
+    def decode_ckks(self, keys: "Keys", ct, scale: float) -> np.ndarray:
+        """Decrypts one ciphertext and decodes its slots on the device."""
+        level = ct.shape[-2]
+        z = np.empty(self.n // 2, dtype=np.complex128)
+        ws = self.workspace(OP_DECODE, level, 1)
+        _check(load().catfhe_decode_ckks(self._h, keys._h, _ptr(ct), level, float(scale),
+                                         z.ctypes.data_as(vp), _ptr(ws), ws.numel(), _stream()),
+               "catfhe_decode_ckks")
+        return z
 
     def mul_plain(self, a, pt, out=None):
         count, _, level, _ = a.shape

@@ -19,6 +19,10 @@ int op_rotate(Context &c, const Keys &keys, const uint64_t *a, uint64_t g, uint6
               const Gather *gth = nullptr);
 int op_plain_import(Context &c, const int64_t *coeffs, uint32_t level, uint64_t *pt,
                     cudaStream_t s);
+int op_encode_ckks(Context &c, const double *slots, double scale, uint32_t level, uint64_t *pt,
+                   void *ws, size_t ws_bytes_in, cudaStream_t s);
+int op_decode_ckks(Context &c, const Keys &k, const uint64_t *ct, uint32_t level, double scale,
+                   double *slots, void *ws, size_t ws_bytes_in, cudaStream_t s);
 int op_mul_plain(Context &c, const uint64_t *a, const uint64_t *pt, uint64_t *out, uint32_t level,
                  uint32_t count, cudaStream_t s);
 int op_rotate_hoisted(Context &c, const Keys &keys, const uint64_t *a, const uint64_t *gs,
@@ -252,6 +256,19 @@ int catfhe_plain_import(catfhe_ctx *ctx, const int64_t *coeffs, uint32_t level, 
                         void *stream) {
     if (!ctx || !coeffs || !pt) return CATFHE_EINVAL;
     return op_plain_import(ctx->c, coeffs, level, pt, S(stream));
+}
+
+int catfhe_encode_ckks(catfhe_ctx *ctx, const double *slots, double scale, uint32_t level,
+                       uint64_t *pt, void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx || !slots || !pt) return CATFHE_EINVAL;
+    return op_encode_ckks(ctx->c, slots, scale, level, pt, ws, ws_bytes, S(stream));
+}
+
+int catfhe_decode_ckks(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *ct,
+                       uint32_t level, double scale, double *slots, void *ws, size_t ws_bytes,
+                       void *stream) {
+    if (!keys_ok(ctx, keys) || !ct || !slots) return CATFHE_EINVAL;
+    return op_decode_ckks(ctx->c, *keys->k, ct, level, scale, slots, ws, ws_bytes, S(stream));
 }
 
 int catfhe_mul_plain(catfhe_ctx *ctx, const uint64_t *a, const uint64_t *pt, uint64_t *out,

@@ -142,6 +142,8 @@ int ctx_init(Context &c, const catfhe_params &p) {
 }
 
 void ctx_free(Context &c) {
+    cudaFree(c.d_enc);
+    cudaFree(c.d_slot);
     cudaFree(c.d_mods);
     cudaFree(c.d_twf);
     cudaFree(c.d_twi);

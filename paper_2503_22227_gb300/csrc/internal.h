@@ -140,6 +140,8 @@ struct Context {
     Scratch scratch;
     int device = 0;
     int ntt_sched = 0;  // NTT schedule index for this ring degree (see ntt.cu)
+    double2 *d_enc = nullptr;   // CKKS encoder tables (encode.cu), built on first use
+    uint32_t *d_slot = nullptr;
 
     int pq(int i) const { return i; }                // index of q_i
     int pp(int k) const { return L + k; }            // index of p_k
@@ -263,6 +265,15 @@ int launch_automorph_ntt_map(const Context &c, const uint64_t *in, uint64_t *out
 // out[ct][p][i] = a[ct][p][i] * pt[i] mod q_i (NTT form), n_limbs = count x 2 x level.
 int launch_mul_plain(const Context &c, const uint64_t *a, const uint64_t *pt, uint64_t *out,
                      uint32_t level, uint32_t n_limbs, cudaStream_t s);
+
+// CKKS canonical embedding on the device (encode.cu).  enc_tables builds
+// the context's tables once; encode: N/2 device slots -> int64 m[N];
+// decode: int64 m[N] -> N/2 device slots.  buf0, buf1: N complex each.
+int enc_tables(Context &c);
+int launch_encode_ckks(const Context &c, const double2 *slots, double scale, double2 *buf0,
+                       double2 *buf1, int64_t *m, cudaStream_t s);
+int launch_decode_ckks(const Context &c, const int64_t *m, double inv_scale, double2 *buf0,
+                       double2 *buf1, double2 *slots, cudaStream_t s);
 int launch_automorph_coeff(const Context &c, const uint64_t *in, uint64_t *out,
                            const LimbMap &map, uint32_t n_limbs, uint64_t g, cudaStream_t s);
 int launch_add(const Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out,

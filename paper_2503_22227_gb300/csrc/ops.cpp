@@ -352,6 +352,17 @@ size_t ws_bytes(const Context &c, int op, uint32_t level, uint32_t count) {
         case CATFHE_OP_EXPORT:
             b.take<uint64_t>(size_t(count) * 2 * level * n);
             break;
+        case CATFHE_OP_ENCODE:
+            b.take<double2>(n / 2);
+            b.take<double2>(2 * n);
+            b.take<int64_t>(n);
+            break;
+        case CATFHE_OP_DECODE:
+            b.take<uint64_t>(size_t(2) * level * n);
+            b.take<int64_t>(n);
+            b.take<double2>(2 * n);
+            b.take<double2>(n / 2);
+            break;
         default:
             return 0;
     }
@@ -1205,18 +1216,15 @@ int op_export(Context &c, const uint64_t *ct, uint32_t level, uint32_t count, in
     return cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
 }
 
-int op_decrypt(Context &c, const Keys &k, const uint64_t *ct, uint32_t level, uint64_t factor,
-               int64_t *msg, void *ws, size_t ws_bytes_in, cudaStream_t s) {
-    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
-    if (c.scheme == CATFHE_BGV && (factor % c.t == 0 || h_invmod(factor % c.t, c.t) == 0))
-        return CATFHE_EINVAL;
-    char *base;
-    TRY(get_ws(c, ws, ws_bytes_in, ws_bytes(c, CATFHE_OP_DECRYPT, level, 1), &base));
+// [c0 + c1 s]_{Q_l} per coefficient (CKKS: centred, two's complement; BFV:
+// round(t x / Q) mod t; BGV: x mod t) into res (device int64[N]), using
+// 2 level N words of scratch at base.
+static int decrypt_device(Context &c, const Keys &k, const uint64_t *ct, uint32_t level,
+                          int64_t *res, char *base, cudaStream_t s) {
     Bump b{base};
     const size_t n = c.n;
     uint64_t *x = b.take<uint64_t>(size_t(level) * n);
     uint64_t *tmp = b.take<uint64_t>(size_t(level) * n);
-    int64_t *res = b.take<int64_t>(n);
     LimbMap m = map_identity(level);
     if (c.scheme != CATFHE_BFV) {
         TRY(launch_mul_add(c, ct, ct + size_t(level) * n, k.s_ntt, x, level, 0, s));
@@ -1247,7 +1255,19 @@ int op_decrypt(Context &c, const Keys &k, const uint64_t *ct, uint32_t level, ui
     }
     PlanList pl;
     TRY(make_list(c, {{key, sp}}, pl));
-    TRY(launch_conv(c, pl, x, 0, 0, reinterpret_cast<uint64_t *>(res), 0, 0, 1, s));
+    return launch_conv(c, pl, x, 0, 0, reinterpret_cast<uint64_t *>(res), 0, 0, 1, s);
+}
+
+int op_decrypt(Context &c, const Keys &k, const uint64_t *ct, uint32_t level, uint64_t factor,
+               int64_t *msg, void *ws, size_t ws_bytes_in, cudaStream_t s) {
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    if (c.scheme == CATFHE_BGV && (factor % c.t == 0 || h_invmod(factor % c.t, c.t) == 0))
+        return CATFHE_EINVAL;
+    char *base;
+    TRY(get_ws(c, ws, ws_bytes_in, ws_bytes(c, CATFHE_OP_DECRYPT, level, 1), &base));
+    const size_t n = c.n;
+    int64_t *res = reinterpret_cast<int64_t *>(base + size_t(2) * level * n * 8);
+    TRY(decrypt_device(c, k, ct, level, res, base, s));
     if (cudaMemcpyAsync(msg, res, n * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CATFHE_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return CATFHE_ECUDA;
     if (c.scheme == CATFHE_BGV) {
@@ -1255,6 +1275,51 @@ int op_decrypt(Context &c, const Keys &k, const uint64_t *ct, uint32_t level, ui
         for (size_t j = 0; j < n; j++) msg[j] = int64_t(h_mulmod(uint64_t(msg[j]), finv, c.t));
     }
     return CATFHE_OK;
+}
+
+// CKKS encode on the device: host slots (N/2 complex) -> plaintext in NTT form.
+int op_encode_ckks(Context &c, const double *slots, double scale, uint32_t level, uint64_t *pt,
+                   void *ws, size_t ws_bytes_in, cudaStream_t s) {
+    if (c.scheme != CATFHE_CKKS) return CATFHE_ESCHEME;
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    if (!(scale > 0)) return CATFHE_EINVAL;
+    TRY(enc_tables(c));
+    char *base;
+    TRY(get_ws(c, ws, ws_bytes_in, ws_bytes(c, CATFHE_OP_ENCODE, level, 1), &base));
+    Bump b{base};
+    const size_t n = c.n;
+    double2 *dz = b.take<double2>(n / 2);
+    double2 *b0 = b.take<double2>(n), *b1 = b.take<double2>(n);
+    int64_t *m = b.take<int64_t>(n);
+    if (cudaMemcpyAsync(dz, slots, n / 2 * sizeof(double2), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return CATFHE_ECUDA;
+    TRY(launch_encode_ckks(c, dz, scale, b0, b1, m, s));
+    LimbMap mp = map_identity(level);
+    TRY(launch_small_to_rns(c, m, pt, mp, level, nullptr, nullptr, 0, s));
+    TRY(launch_ntt_fwd(c, pt, pt, mp, level, s));
+    return cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
+}
+
+// CKKS decrypt + decode: ciphertext -> host slots (N/2 complex) / scale.
+int op_decode_ckks(Context &c, const Keys &k, const uint64_t *ct, uint32_t level, double scale,
+                   double *slots, void *ws, size_t ws_bytes_in, cudaStream_t s) {
+    if (c.scheme != CATFHE_CKKS) return CATFHE_ESCHEME;
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    if (!(scale > 0)) return CATFHE_EINVAL;
+    TRY(enc_tables(c));
+    char *base;
+    TRY(get_ws(c, ws, ws_bytes_in, ws_bytes(c, CATFHE_OP_DECODE, level, 1), &base));
+    Bump b{base};
+    const size_t n = c.n;
+    char *dec = reinterpret_cast<char *>(b.take<uint64_t>(size_t(2) * level * n));
+    int64_t *m = b.take<int64_t>(n);
+    double2 *b0 = b.take<double2>(n), *b1 = b.take<double2>(n);
+    double2 *dz = b.take<double2>(n / 2);
+    TRY(decrypt_device(c, k, ct, level, m, dec, s));
+    TRY(launch_decode_ckks(c, m, 1.0 / scale, b0, b1, dz, s));
+    if (cudaMemcpyAsync(slots, dz, n / 2 * sizeof(double2), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return CATFHE_ECUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
 }
 
 }  // namespace catfhe
