@@ -328,6 +328,17 @@ def serving_sweep(W, fracs=(0.1, 0.5, 0.8, 1.5), lanes=8, max_active=64):
         points.append({"offered_per_s": rate, "requests": count, "throughput_per_s": st.throughput,
                        **st.latency, "mean_active": st.mean_active, "max_active": st.max_active,
                        "joined_running_batch": st.admitted_while_busy, "ticks": st.ticks})
+    # search-and-average: circuit (sum and count) + two-party inverse + HMult,
+    # one query at a time, wall time including the client's decrypt/encrypt
+    import numpy as np
+    avg_ms = []
+    for k in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.search_and_average(table, k % S.COLS, (k + 1) % S.COLS, k % len(table.bounds),
+                             rng=np.random.default_rng(k))
+        torch.cuda.synchronize()
+        avg_ms.append((time.perf_counter() - t0) * 1e3)
     counts = table.circuit.counts()
     head = points[1] if len(points) > 1 else points[0]
     out = {"unit": "queries/s", "saturation_per_s": mu,
@@ -338,6 +349,10 @@ def serving_sweep(W, fracs=(0.1, 0.5, 0.8, 1.5), lanes=8, max_active=64):
            "request": {"rows": S.ROWS, "columns": S.COLS, "stages": len(table.circuit.stages()),
                        "ops": {k: v for k, v in counts.items() if k != "input"},
                        "reserved_bytes": table.need},
+           "search_and_average_ms": {"first": avg_ms[0], "median_of_rest": float(np.median(avg_ms[1:])),
+                                     "note": "Avg(b) where lo <= a <= hi: sum and count circuit, the "
+                                             "two-party multiply-inverse (client decrypts the masked "
+                                             "count, inverts, re-encrypts), one HMult; one query alone"},
            "budget_bytes": budget, "max_active": max_active, "lanes": lanes,
            "note": "latency from Poisson arrival to the encrypted answer in pinned host memory; "
                    "p50/p99 at the second sweep point (0.5 x saturation)"}

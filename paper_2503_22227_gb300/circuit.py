@@ -358,12 +358,14 @@ class Runner:
 
 
 def pdq_circuit(ctx, delta: float, coeffs, kappa: float = 1.0, sum_slots: int = 1024,
-                galois=None) -> Circuit:
+                galois=None, with_count: bool = False) -> Circuit:
     """The range-predicate masked sum: with x = column a, y = column b and
     encrypted bounds lo, hi,
         u = kappa (x - lo), v = kappa (hi - x),
         mask = (1 + p(u)) (1 + p(v)) / 4,  p ~ sign (Chebyshev coefficients),
-        out = sum over slots 0 .. sum_slots-1 of mask * y (rotate-and-add)."""
+        out = sum over slots 0 .. sum_slots-1 of mask * y (rotate-and-add).
+    with_count adds the input "ones" (1 in the table's rows) and the output
+    "count" = the same sum of mask * ones, for the search-and-average query."""
     c = Circuit(ctx.q, delta, int(np.log2(ctx.n)))
     L = ctx.L
     x, y = c.input("x", L), c.input("y", L)
@@ -374,11 +376,16 @@ def pdq_circuit(ctx, delta: float, coeffs, kappa: float = 1.0, sum_slots: int = 
     pu, pv = c.chebyshev(d1, coeffs), c.chebyshev(d2, coeffs)
     mask = c.mul(c.add_const(pu, 1.0), c.add_const(pv, 1.0))
     mask = c.scalar(mask, 0.25)
-    s = c.mul(mask, y)
-    r = 1
-    while r < sum_slots:
-        g = galois[r] if galois is not None else ctx.galois_elt(r)
-        s = c.add(s, c.rotate(s, r, g))
-        r *= 2
-    c.output("sum", s)
+    def slot_sum(t):
+        r = 1
+        while r < sum_slots:
+            g = galois[r] if galois is not None else ctx.galois_elt(r)
+            t = c.add(t, c.rotate(t, r, g))
+            r *= 2
+        return t
+
+    c.output("sum", slot_sum(c.mul(mask, y)))
+    if with_count:
+        ones = c.input("ones", L)
+        c.output("count", slot_sum(c.mul(mask, ones)))
     return c

@@ -227,6 +227,11 @@ class Table:
         self.slots[:, :ROWS] = self.values
         self.columns = [ctx.encrypt(self.keys, encoding.encode(self.slots[c], ctx.n, self.delta),
                                     W.seed_for(f"{seed}-col{c}")) for c in range(COLS)]
+        self.ones_slots = np.zeros(ctx.n // 2)
+        self.ones_slots[:ROWS] = 1.0
+        self.ones = ctx.encrypt(self.keys, encoding.encode(self.ones_slots, ctx.n, self.delta),
+                                W.seed_for(f"{seed}-ones"))
+        self.seed = seed
         self.circuit = circuit.pdq_circuit(ctx, self.delta, sign_coefficients(), kappa=kappa,
                                            sum_slots=SUM_SLOTS, galois=self.galois)
         brng = W.rng_for(seed + "-bounds")
@@ -248,6 +253,14 @@ class Table:
         self.ct_bytes = 2 * ctx.L * ctx.n * 8
         self.need = self.circuit.peak_bytes() + 2 * self.ct_bytes
 
+    def avg_circuit(self):
+        if getattr(self, "_avg_circuit", None) is None:
+            from . import circuit
+            self._avg_circuit = circuit.pdq_circuit(self.ctx, self.delta, sign_coefficients(),
+                                                    sum_slots=SUM_SLOTS, galois=self.galois,
+                                                    with_count=True)
+        return self._avg_circuit
+
     def float_answer(self, col_a: int, col_b: int, bounds: int) -> float:
         """The float64 evaluation of the same circuit (same integer constants
         and scales) on the plaintext slots; slot 0 holds the sum."""
@@ -258,6 +271,18 @@ class Table:
         out = self.circuit.evaluate_float({"x": self.slots[col_a], "y": self.slots[col_b],
                                            "lo": np.full(half, lo_v), "hi": np.full(half, hi_v)})
         return float(out["sum"][0].real)
+
+    def float_avg_parts(self, col_a: int, col_b: int, bounds: int) -> tuple:
+        """(sum, count) of the search-and-average circuit evaluated in float64
+        with the same integer constants and scales."""
+        lo, hi = self.bounds[bounds]
+        lo_v = self.encoding.encode_constant(lo, self.delta) / self.delta
+        hi_v = self.encoding.encode_constant(hi, self.delta) / self.delta
+        half = self.ctx.n // 2
+        out = self.avg_circuit().evaluate_float(
+            {"x": self.slots[col_a], "y": self.slots[col_b], "ones": self.ones_slots,
+             "lo": np.full(half, lo_v), "hi": np.full(half, hi_v)})
+        return float(out["sum"][0].real), float(out["count"][0].real)
 
     def decrypt_answer(self, result_host) -> float:
         """Client side: decrypt and decode slot 0 of a host result."""
@@ -382,3 +407,72 @@ def make_requests(table: Table, count: int, rate: float, seed: str) -> list:
         out.append(Request(id=i, arrival=float(t[i]), col_a=int(a), col_b=int(b),
                            bounds=int(rng.integers(len(table.uploads)))))
     return out
+
+
+# --------------------------------------------------------------------------- search-and-average
+def _scalar(ctx, ct, r: float):
+    """Server-side multiplication by the real r at unchanged scale: the
+    integer k = round(r q_top) then a rescale by q_top; returns the
+    ciphertext and the multiplier k / q_top it actually applied."""
+    level = ct.shape[-2]
+    q = ctx.q[level - 1]
+    k = int(round(r * q))
+    return ctx.rescale(ctx.mul_int(ct, k)), k / q
+
+
+def multiply_inverse(table: Table, ct, scale: float, rng) -> tuple:
+    """The two-party multiply-inverse (the paper's Algorithm 2), slot 0:
+    the server masks Enc(x) by a random real r and sends Enc(r x); the
+    client decrypts, inverts and sends back Enc(1 / (r x)) (a fresh
+    encryption of the constant); the server multiplies by r again, leaving
+    Enc(1 / x).  Returns (Enc(1/x), the masked value the client saw)."""
+    ctx, keys, enc = table.ctx, table.keys, table.encoding
+    r = float(rng.uniform(0.5, 2.0))
+    c1, r_eff = _scalar(ctx, ct, r)                                # server
+    x1 = float(ctx.decode_ckks(keys, c1, scale)[0].real)           # client
+    m = np.zeros(ctx.n, dtype=np.int64)
+    m[0] = enc.encode_constant(1.0 / x1, table.delta)
+    c2 = ctx.encrypt(keys, m, W.seed_for(f"{table.seed}-inv-{rng.integers(1 << 62)}"))
+    c3, _ = _scalar(ctx, c2, r_eff)                                # server
+    return c3, x1
+
+
+def search_and_average(table: Table, col_a: int, col_b: int, bounds: int, rng=None) -> dict:
+    """Avg(column b) where lo <= column a <= hi (soft predicate): the circuit
+    computes Enc(sum of mask * b) and Enc(sum of mask) together, the
+    multiply-inverse turns the count into Enc(1 / count), one HMult gives
+    the average; returns the decrypted average and the intermediate values."""
+    from . import api, circuit
+    ctx, keys = table.ctx, table.keys
+    rng = rng or W.rng_for(f"{table.seed}-avg")
+    c = table.avg_circuit()
+    lo_h, hi_h = table.uploads[bounds]
+    inputs = {"x": table.columns[col_a], "y": table.columns[col_b], "ones": table.ones,
+              "lo": ctx.import_ct(lo_h, api.FORM_NATIVE), "hi": ctx.import_ct(hi_h, api.FORM_NATIVE)}
+    run = circuit.Runner(c, ctx, keys, inputs)
+    ws = None
+    while not run.done:
+        ops = run.stage_ops()
+        batch = api.Batch(ops)
+        need = batch.workspace_bytes(8)
+        if ws is None or ws.numel() < need:
+            ws = table.torch.empty(need, dtype=table.torch.uint8, device="cuda")
+        batch.run(8, ws)
+        run.advance()
+    s_ct, n_ct = run.result("sum"), run.result("count")
+    s_scale = c.nodes[c.outputs["sum"]].scale
+    n_scale = c.nodes[c.outputs["count"]].scale
+    inv, masked = multiply_inverse(table, n_ct, n_scale, rng)
+    # bring 1/count down to the sum's level, then one HMult + rescale
+    lv = s_ct.shape[-2]
+    if inv.shape[-2] > lv:
+        inv = ctx.drop_level(inv, lv)
+    elif inv.shape[-2] < lv:
+        s_ct = ctx.drop_level(s_ct, inv.shape[-2])
+        lv = inv.shape[-2]
+    avg_ct = ctx.mul_relin_rescale(keys, s_ct, inv)
+    avg_scale = s_scale * table.delta / ctx.q[lv - 1]
+    avg = float(ctx.decode_ckks(keys, avg_ct, avg_scale)[0].real)
+    return {"avg": avg, "masked_count_seen_by_client": masked,
+            "sum": float(ctx.decode_ckks(keys, s_ct, s_scale)[0].real),
+            "count": float(ctx.decode_ckks(keys, n_ct, n_scale)[0].real)}

@@ -66,3 +66,23 @@ def test_admission_by_memory(table):
     assert st.max_active == 2 and st.served == 5
     with pytest.raises(ValueError):
         S.serve(S.make_requests(table, 1, 0.0, "x"), eng, budget_bytes=table.need - 1)
+
+
+def test_search_and_average(table):
+    """Avg(b) where lo <= a <= hi: the circuit's encrypted sum and count, the
+    two-party multiply-inverse on the count (the client only sees the count
+    times a random mask), one HMult; against the same soft predicate in numpy."""
+    res = S.search_and_average(table, 2, 3, 1, rng=np.random.default_rng(11))
+    total, count = table.float_avg_parts(2, 3, 1)
+    assert abs(res["count"] - count) < 1000 * 2.0 ** -20
+    assert abs(res["sum"] - total) < 1000 * 2.0 ** -20
+    assert abs(res["avg"] - total / count) < 1e-7
+    assert abs(res["masked_count_seen_by_client"] - count) > 1e-3
+    # the float circuit itself is the soft predicate up to the scale drift of
+    # the prime chain (relative 1e-4)
+    lo, hi = table.bounds[1]
+    a, b = table.values[2], table.values[3]
+    p = lambda x: np.polynomial.chebyshev.chebval(x, S.sign_coefficients())
+    mask = (1 + p(a - lo)) * (1 + p(hi - a)) / 4
+    assert abs(count - mask.sum()) < 1e-4 * mask.sum()
+    assert abs(total / count - (mask * b).sum() / mask.sum()) < 1e-4
