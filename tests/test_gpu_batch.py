@@ -157,3 +157,67 @@ def test_compatible_entries_are_merged_and_exact():
     torch.cuda.synchronize()
     for j, (o, w) in enumerate(zip(outs, wants)):
         assert torch.equal(o, w), ("graph", j)
+
+
+@pytest.mark.slow
+def test_uneven_mix_full_sizes_sampled():
+    """The uneven mix at its real sizes (N from 2^13 to 2^16 on one prime
+    chain, levels 2..24, HMult+relin / HRotate / rescale, tuned NTT schedules,
+    one captured graph over 8 lanes), 48 operations: every output equals the
+    single call, and two N = 2^13 outputs equal the oracle."""
+    base = W.PRESETS["ckks_n16"]
+    rng = W.rng_for("mix-test")
+    ctxs = {}
+    for log_n in (13, 14, 15, 16):
+        pr = W.Preset(f"mix_n{log_n}", W.CKKS, log_n, base.q_bits, base.p_bits, base.dnum,
+                      log_n_max=16)
+        c = api.Context(pr)
+        k = c.keygen(W.seed_for(f"mix-keys-{log_n}"))
+        gs = [c.galois_elt(r) for r in (1, 7)]
+        for g in gs:
+            k.gen_galois(g)
+        c.tune_ntt(2 * c.L * 2)
+        ctxs[log_n] = (pr, c, k, gs)
+    kinds = [api.OP_MUL_RELIN, api.OP_ROTATE, api.OP_RESCALE]
+    seed = W.seed_for("mix-test-inputs")
+    ops, outs, wants, meta = [], [], [], []
+    for i in range(48):
+        log_n = int(rng.choice([13, 14, 15, 16]))
+        level = int(rng.integers(2, 25))
+        kind = kinds[i % 3]
+        pr, c, k, gs = ctxs[log_n]
+        g = gs[i % 2]
+        a = c.ct_uniform(seed, 2 * i, level)
+        b = c.ct_uniform(seed, 2 * i + 1, level)
+        if kind == api.OP_MUL_RELIN:
+            want = c.mul_relin(k, a, b)
+        elif kind == api.OP_ROTATE:
+            want = c.rotate(k, a, g)
+        else:
+            want = c.rescale(a)
+        out = torch.full_like(want, -1)
+        ops.append(api.make_op(kind, c, a, out, keys=k, b=b, galois_elt=g))
+        outs.append(out)
+        wants.append(want.clone())
+        meta.append((log_n, level, kind, i, g, a, b))
+    graph = api.Graph(ops, lanes=8)
+    graph.launch()
+    torch.cuda.synchronize()
+    for j, (o, w) in enumerate(zip(outs, wants)):
+        assert torch.equal(o, w), j
+    checked = 0
+    for (log_n, level, kind, i, g, a, b), o in zip(meta, outs):
+        if log_n != 13 or kind == api.OP_RESCALE or checked >= 2:
+            continue
+        pr, c, k, gs = ctxs[13]
+        oc = oracle.Context(pr.scheme, pr.log_n, pr.q_bits, pr.p_bits, pr.dnum, log_n_max=16)
+        ok = oc.keygen(W.seed_for("mix-keys-13"))
+        oa, ob = oc.ct_uniform(seed, 2 * i, level), oc.ct_uniform(seed, 2 * i + 1, level)
+        if kind == api.OP_MUL_RELIN:
+            want = oc.mul_relin(ok, oa, ob)
+        else:
+            ok.gen_galois(g)
+            want = oc.rotate(ok, oa, g)
+        assert np.array_equal(c.export_ct(o)[0], want), (kind, level)
+        checked += 1
+    assert checked == 2

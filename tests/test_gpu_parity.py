@@ -310,13 +310,21 @@ def test_integer_schemes_match_oracle(preset):
 
 @pytest.mark.parametrize("name", ["bfv_n14", "bgv_n14"])
 def test_integer_schemes_full_size(name):
-    """The N = 2^14, 8 x 55-bit chain, t = 65537, batch of 2 (full shape)."""
+    """The N = 2^14, 8 x 55-bit chain, t = 65537 in the benchmark's launch
+    configuration: one HMult+relin launch over the batch of 16 pairs (the
+    benchmark's seeds and keys); the first and last outputs checked limb for
+    limb against the oracle."""
     p = W.PRESETS[name]
-    pr = Pair(p)
-    a, b = _uniform_pair(pr, p.L, 2, "full-" + name)
-    got = pr.g.export_ct(pr.g.mul_relin(pr.gk, pr.g.import_ct(a), pr.g.import_ct(b)))
-    for c in range(2):
-        assert np.array_equal(got[c], pr.o.mul_relin(pr.ok, a[c], b[c])), c
+    g_ctx, o_ctx = api.Context(p), octx_for(p)
+    gk = g_ctx.keygen(W.seed_for("bench-keys-" + name))
+    ok = o_ctx.keygen(W.seed_for("bench-keys-" + name))
+    seed = W.seed_for("bench-inputs-" + name)
+    x = torch.cat([g_ctx.ct_uniform(seed, 2 * i, p.L) for i in range(p.batch)])
+    y = torch.cat([g_ctx.ct_uniform(seed, 2 * i + 1, p.L) for i in range(p.batch)])
+    got = g_ctx.export_ct(g_ctx.mul_relin(gk, x, y))
+    for i in (0, p.batch - 1):
+        oa, ob = o_ctx.ct_uniform(seed, 2 * i, p.L), o_ctx.ct_uniform(seed, 2 * i + 1, p.L)
+        assert np.array_equal(got[i], o_ctx.mul_relin(ok, oa, ob)), i
 
 
 @pytest.mark.slow
