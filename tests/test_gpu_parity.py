@@ -488,3 +488,32 @@ def test_mul_plain_matches_oracle(preset):
     with pytest.raises(api.CatfheError) as e:
         bfv.g.plain_import(pt, SMALL_BFV.L)
     assert e.value.code == -6
+
+
+def test_zero_count_is_a_noop(ckks12):
+    """count = 0 with valid buffers enqueues nothing and leaves out untouched."""
+    import ctypes
+    pr = ckks12
+    L = api.load()
+    a = pr.g.ct_uniform(W.seed_for("zero"), 0, 3)
+    out = torch.full_like(a, 7)
+    ws = pr.g.workspace(api.OP_MUL_RELIN_RESCALE, 3, 1)
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    h, kh = pr.g._h, pr.gk._h
+    g = pr.g.galois_elt(1)
+    rcs = [
+        L.catfhe_mul_relin(h, kh, P(a), P(a), P(out), 3, 0, P(ws), ws.numel(), s),
+        L.catfhe_mul_relin_rescale(h, kh, P(a), P(a), P(out), 3, 0, P(ws), ws.numel(), s),
+        L.catfhe_rotate(h, kh, P(a), g, P(out), 3, 0, P(ws), ws.numel(), s),
+        L.catfhe_rescale(h, P(a), P(out), 3, 0, P(ws), ws.numel(), s),
+        L.catfhe_add(h, P(a), P(a), P(out), 3, 0, s),
+        L.catfhe_sub(h, P(a), P(a), P(out), 3, 0, s),
+        L.catfhe_mul_int(h, P(a), 5, P(out), 3, 0, s),
+        L.catfhe_add_const(h, P(a), 5, P(out), 3, 0, s),
+        L.catfhe_drop_level(h, P(a), 3, 2, P(out), 0, s),
+        L.catfhe_mul_plain(h, P(a), P(a), P(out), 3, 0, s),
+    ]
+    assert rcs == [0] * len(rcs)
+    torch.cuda.synchronize()
+    assert bool((out == 7).all())
