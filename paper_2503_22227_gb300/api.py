@@ -41,7 +41,7 @@ EXPORTS = [
     "catfhe_tune_ntt", "catfhe_ntt_schedule", "catfhe_set_ntt_schedule",
     "catfhe_sub", "catfhe_mul_int", "catfhe_add_const", "catfhe_drop_level",
     "catfhe_rotate_hoisted", "catfhe_plain_import", "catfhe_mul_plain",
-    "catfhe_encode_ckks", "catfhe_decode_ckks",
+    "catfhe_encode_ckks", "catfhe_decode_ckks", "catfhe_device_status", "catfhe_wait_selftest",
 ]
 
 
@@ -110,6 +110,8 @@ def load(path: str = LIB_PATH):
             "catfhe_plain_import": (ctypes.c_int, [vp, vp, u32, vp, vp]),
             "catfhe_mul_plain": (ctypes.c_int, [vp, vp, vp, vp, u32, u32, vp]),
             "catfhe_encode_ckks": (ctypes.c_int, [vp, vp, ctypes.c_double, u32, vp, vp, sz, vp]),
+            "catfhe_device_status": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int, vp]),
+            "catfhe_wait_selftest": (ctypes.c_int, [vp, u64, vp]),
             "catfhe_decode_ckks": (ctypes.c_int, [vp, vp, vp, u32, ctypes.c_double, vp, vp, sz, vp]),
             "catfhe_rescale": (ctypes.c_int, [vp, vp, vp, u32, u32, vp, sz, vp]),
             "catfhe_decrypt": (ctypes.c_int, [vp, vp, vp, u32, u64, vp, vp, sz, vp]),
@@ -393,6 +395,16 @@ class Context:
                                          z.ctypes.data_as(vp), _ptr(ws), ws.numel(), _stream()),
                "catfhe_decode_ckks")
         return z
+
+    def device_status(self, clear: bool = True) -> int:
+        """Status word of the kernels' bounded waits (0: none timed out)."""
+        v = ctypes.c_int32(0)
+        _check(load().catfhe_device_status(self._h, ctypes.byref(v), 1 if clear else 0, _stream()),
+               "catfhe_device_status")
+        return v.value
+
+    def wait_selftest(self, limit_ns: int = 20_000_000) -> None:
+        _check(load().catfhe_wait_selftest(self._h, int(limit_ns), _stream()), "catfhe_wait_selftest")
 
     def mul_plain(self, a, pt, out=None):
         count, _, level, _ = a.shape

@@ -252,6 +252,24 @@ int catfhe_rotate(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
     return op_rotate(ctx->c, *keys->k, a, galois_elt, out, level, count, ws, ws_bytes, S(stream));
 }
 
+int catfhe_device_status(catfhe_ctx *ctx, int32_t *flags, int clear, void *stream) {
+    if (!ctx || !flags) return CATFHE_EINVAL;
+    cudaStream_t s = S(stream);
+    int v = 0;
+    if (cudaMemcpyAsync(&v, ctx->c.d_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return CATFHE_ECUDA;
+    if (clear && cudaMemsetAsync(ctx->c.d_status, 0, sizeof(int), s) != cudaSuccess)
+        return CATFHE_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CATFHE_ECUDA;
+    *flags = v;
+    return CATFHE_OK;
+}
+
+int catfhe_wait_selftest(catfhe_ctx *ctx, uint64_t limit_ns, void *stream) {
+    if (!ctx || limit_ns < 1000 || limit_ns > 10000000000ull) return CATFHE_EINVAL;
+    return launch_wait_selftest(ctx->c, limit_ns, S(stream));
+}
+
 int catfhe_plain_import(catfhe_ctx *ctx, const int64_t *coeffs, uint32_t level, uint64_t *pt,
                         void *stream) {
     if (!ctx || !coeffs || !pt) return CATFHE_EINVAL;

@@ -132,6 +132,8 @@ int ctx_init(Context &c, const catfhe_params &p) {
     }
     h_cdt(c.cdt);
     if (cudaGetDevice(&c.device) != cudaSuccess) return CATFHE_ECUDA;
+    if (cudaMalloc(&c.d_status, sizeof(int)) != cudaSuccess) return CATFHE_ENOMEM;
+    if (cudaMemset(c.d_status, 0, sizeof(int)) != cudaSuccess) return CATFHE_ECUDA;
     if (cudaMalloc(&c.d_mods, sizeof(DevMod) * np) != cudaSuccess) return CATFHE_ENOMEM;
     if (cudaMalloc(&c.d_twf, sizeof(ulonglong2) * np * n) != cudaSuccess) return CATFHE_ENOMEM;
     if (cudaMalloc(&c.d_twi, sizeof(ulonglong2) * np * n) != cudaSuccess) return CATFHE_ENOMEM;
@@ -142,6 +144,7 @@ int ctx_init(Context &c, const catfhe_params &p) {
 }
 
 void ctx_free(Context &c) {
+    cudaFree(c.d_status);
     cudaFree(c.d_enc);
     cudaFree(c.d_slot);
     cudaFree(c.d_mods);

@@ -6,6 +6,7 @@
 // All are HBM-bound streams over limb-major data: one thread per coefficient,
 // consecutive threads on consecutive words, grids sized by the data (a whole
 // batch of ciphertexts per launch).
+#include "bulk.cuh"
 #include "modarith.cuh"
 
 namespace catfhe {
@@ -164,7 +165,166 @@ k_ip_stream(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
         csub(redc(b1, m.q, m.qinv), m.q));
 }
 
+// Inner product with bulk-copy staging: a CTA owns one extended limb i and
+// a tile of kIpTile coefficients for every ciphertext of the batch.  Thread
+// 0 loads the tile of the 2 BETA key rows once (bulk copies into shared
+// memory) and streams each ciphertext's digit (and fold) tiles through two
+// shared buffers, the next ciphertext's copies in flight while the threads
+// compute on the current one; all threads then read shared memory only.
+// Used when every address is 16-byte aligned (bulk-copy rule) and
+// BETA <= 4; same arithmetic as k_ip, bit for bit.
+constexpr uint32_t kIpTile = 512;
+
+template <int BETA>
+__global__ void __launch_bounds__(256)
+k_ip_bulk(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n, uint32_t count) {
+    extern __shared__ __align__(128) uint64_t sm[];
+    __shared__ __align__(8) uint64_t bars[3];  // buffer 0, buffer 1, keys
+    const size_t n = size_t(1) << log_n;
+    const uint32_t i = blockIdx.y, tid = threadIdx.x;
+    const size_t x0 = size_t(blockIdx.x) * kIpTile;
+    const uint32_t beta = A.beta, KL = A.L + A.K;
+    const DevMod m = mods[A.prime[i]];
+    const bool fold = i < A.level && A.pfac[i] != 0;
+    const bool f0 = fold && A.add0, f1 = fold && A.add1;
+    const uint32_t own_digit = (A.own != nullptr && i < A.level) ? i / A.alpha : 0xffffffffu;
+    constexpr uint32_t TB = kIpTile * 8;  // bytes per tile
+    uint64_t *skey = sm;                                   // [2 BETA][tile]
+    uint64_t *sbuf[2] = {sm + 2 * BETA * kIpTile, sm + (3 * BETA + 2) * kIpTile};
+    const uint32_t item_bytes = (beta + (f0 ? 1 : 0) + (f1 ? 1 : 0)) * TB;
+
+    auto issue_item = [&](uint32_t item, uint32_t b) {
+        uint64_t *dst = sbuf[b];
+        mbar_expect_tx(&bars[b], item_bytes);
+        const uint64_t *ext = A.ext + item * A.ext_item;
+        for (uint32_t j = 0; j < beta; j++) {
+            const uint64_t *src = (j == own_digit) ? A.own + item * A.own_item + size_t(i) * n
+                                                   : ext + (size_t(j) * A.M + i) * n;
+            bulk_load(dst + j * kIpTile, src + x0, TB, &bars[b]);
+        }
+        if (f0) bulk_load(dst + BETA * kIpTile, A.add0 + item * A.add_item + size_t(i) * n + x0, TB, &bars[b]);
+        if (f1) bulk_load(dst + (BETA + 1) * kIpTile, A.add1 + item * A.add_item + size_t(i) * n + x0, TB, &bars[b]);
+    };
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(&bars[2], 2 * beta * TB);
+        for (uint32_t j = 0; j < beta; j++) {
+            bulk_load(skey + (2 * j) * kIpTile, A.key + ((size_t(j) * 2 + 0) * KL + A.key_limb[i]) * n + x0, TB, &bars[2]);
+            bulk_load(skey + (2 * j + 1) * kIpTile, A.key + ((size_t(j) * 2 + 1) * KL + A.key_limb[i]) * n + x0, TB, &bars[2]);
+        }
+        issue_item(0, 0);
+        if (count > 1) issue_item(1, 1);
+    }
+    // every wait is bounded, and the CTA decides together whether to go on
+    // (__syncthreads_and), so no thread is left waiting at a barrier
+    bool ok = __syncthreads_and(mbar_wait(&bars[2], 0));
+    const uint32_t u = 2 * tid;  // this thread's two coefficients in the tile
+    for (uint32_t item = 0; item < count && ok; item++) {
+        const uint32_t b = item & 1;
+        ok = __syncthreads_and(mbar_wait(&bars[b], (item >> 1) & 1));
+        if (!ok) break;
+        const uint64_t *buf = sbuf[b];
+        U128 a0{0, 0}, a1{0, 0}, b0{0, 0}, b1{0, 0};
+        if (f0) {
+            const ulonglong2 d = ld2(buf + BETA * kIpTile + u);
+            mac(a0, d.x, A.pfac[i]);
+            mac(a1, d.y, A.pfac[i]);
+        }
+        if (f1) {
+            const ulonglong2 d = ld2(buf + (BETA + 1) * kIpTile + u);
+            mac(b0, d.x, A.pfac[i]);
+            mac(b1, d.y, A.pfac[i]);
+        }
+#pragma unroll
+        for (int j = 0; j < BETA; j++) {
+            if (uint32_t(j) < beta) {
+                const ulonglong2 c = ld2(buf + j * kIpTile + u);
+                const ulonglong2 kb = ld2(skey + (2 * j) * kIpTile + u);
+                const ulonglong2 ka = ld2(skey + (2 * j + 1) * kIpTile + u);
+                mac(a0, c.x, kb.x);
+                mac(a1, c.y, kb.y);
+                mac(b0, c.x, ka.x);
+                mac(b1, c.y, ka.y);
+            }
+        }
+        uint64_t *y = A.y + item * A.y_item + x0 + u;
+        st2(y + size_t(i) * n, csub(redc(a0, m.q, m.qinv), m.q), csub(redc(a1, m.q, m.qinv), m.q));
+        st2(y + (size_t(A.M) + i) * n, csub(redc(b0, m.q, m.qinv), m.q),
+            csub(redc(b1, m.q, m.qinv), m.q));
+        __syncthreads();  // everyone is done with buffer b
+        if (tid == 0 && item + 2 < count) {
+            fence_proxy_async();
+            issue_item(item + 2, b);
+        }
+    }
+    if (!ok && tid == 0) {
+        atomicOr(A.status, kStatusIpWait);
+        // give this CTA's copies still in flight a bounded time to land
+        mbar_wait(&bars[0], 0);
+        mbar_wait(&bars[1], 0);
+    }
+}
+
+// Watchdog self-test: a barrier that expects 16 bytes of bulk-copy data that
+// no copy ever brings; the bounded wait must give up after limit_ns and the
+// kernel must report it in the status word and return.
+__global__ void k_wait_selftest(int *status, uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_expect_tx(&bar, 16);
+    const bool ok = __syncthreads_and(mbar_wait(&bar, 0, limit_ns));
+    if (!ok && threadIdx.x == 0) atomicOr(status, kStatusSelfTestWait);
+}
+
+int launch_wait_selftest(const Context &c, uint64_t limit_ns, cudaStream_t s) {
+    k_wait_selftest<<<1, 64, 0, s>>>(c.d_status, limit_ns);
+    return ok();
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+static int launch_ip_regs(const Context &c, const IpArgs &a, uint32_t count, cudaStream_t s);
+
 int launch_ip(const Context &c, const IpArgs &a, uint32_t count, cudaStream_t s) {
+    const size_t n = c.n;
+    bool bulk = a.beta <= 4 && a.status != nullptr && n % kIpTile == 0 && aligned16(a.ext) &&
+                aligned16(a.key) && aligned16(a.y) && (!a.own || aligned16(a.own)) &&
+                (!a.add0 || aligned16(a.add0)) && (!a.add1 || aligned16(a.add1)) &&
+                (a.ext_item * 8) % 16 == 0 && (a.own_item * 8) % 16 == 0 &&
+                (a.add_item * 8) % 16 == 0 && (a.y_item * 8) % 16 == 0;
+    if (bulk) {
+        const dim3 g(unsigned(n / kIpTile), a.M);
+        switch (a.beta) {
+#define IPB(B)                                                                                   \
+    case B: {                                                                                    \
+        const size_t smb = size_t(4 * B + 4) * kIpTile * 8;                                      \
+        if (cudaFuncSetAttribute(k_ip_bulk<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                 int(smb)) != cudaSuccess)                                       \
+            return CATFHE_ECUDA;                                                                 \
+        k_ip_bulk<B><<<g, 256, smb, s>>>(a, c.d_mods, c.log_n, count);                           \
+        break;                                                                                   \
+    }
+            IPB(1) IPB(2) IPB(3) IPB(4)
+#undef IPB
+            default: bulk = false;
+        }
+        if (bulk) return ok();
+    }
+    return launch_ip_regs(c, a, count, s);
+}
+
+static int launch_ip_regs(const Context &c, const IpArgs &a, uint32_t count, cudaStream_t s) {
     const dim3 g(count, unsigned((c.n / 2 + 255) / 256), a.M);
     switch (a.beta) {
         case 1: k_ip<1><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n); break;

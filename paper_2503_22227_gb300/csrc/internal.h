@@ -140,6 +140,7 @@ struct Context {
     Scratch scratch;
     int device = 0;
     int ntt_sched = 0;  // NTT schedule index for this ring degree (see ntt.cu)
+    int *d_status = nullptr;    // device status word: bits of kernels' timed-out waits
     double2 *d_enc = nullptr;   // CKKS encoder tables (encode.cu), built on first use
     uint32_t *d_slot = nullptr;
 
@@ -241,8 +242,10 @@ struct IpArgs {
     uint8_t prime[kMapMax];    // prime of position i
     uint16_t key_limb[kMapMax];
     uint64_t pfac[kMapMax];    // P 2^64 mod prime(i) (0 for P positions)
+    int *status;               // the context's status word (bulk-copy wait timeouts)
 };
 int launch_ip(const Context &c, const IpArgs &a, uint32_t count, cudaStream_t s);
+int launch_wait_selftest(const Context &c, uint64_t limit_ns, cudaStream_t s);
 
 struct CombineArgs {
     const uint64_t *y;         // [count][2][.][N] at y_off positions

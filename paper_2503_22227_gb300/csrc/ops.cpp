@@ -178,6 +178,7 @@ static int inner_product(Context &c, const uint64_t *ext, const uint64_t *own, c
     a.L = c.L;
     a.K = c.K;
     a.alpha = c.alpha;
+    a.status = c.d_status;
     for (int i = 0; i < M; i++) {
         const int gp = ext_prime(c, level, i);
         a.prime[i] = uint8_t(gp);
