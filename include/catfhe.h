@@ -337,12 +337,12 @@ int catfhe_ntt(catfhe_ctx *ctx, uint64_t *limbs, uint32_t level, uint32_t count,
 /* Kernel watchdog.  Kernels that wait on an mbarrier for bulk copies bound
  * every wait (about one second of global time); on timeout they set a bit in
  * the context's device status word and return instead of waiting on (bit 1:
- * the inner product's copies; bit 2: catfhe_wait_selftest).  The paper has no
- * counterpart.  catfhe_device_status synchronises `stream`, stores the word
- * in *flags and clears it if `clear`.  catfhe_wait_selftest launches one CTA
- * whose barrier expects data that never comes: its wait gives up after
- * limit_ns nanoseconds (1e3 .. 1e10) and sets bit 2, so a caller can check
- * that a timed-out wait ends and is reported. */
+ * the inner product's copies; bit 2: catfhe_wait_selftest).  The paper has
+ * no counterpart.  catfhe_device_status synchronises `stream`, stores the
+ * word in *flags and clears it if `clear`.  catfhe_wait_selftest launches
+ * one CTA whose barrier expects data that never comes: its wait gives up
+ * after limit_ns nanoseconds (1e3 .. 1e10) and sets bit 2, so a caller can
+ * check that a timed-out wait ends and is reported. */
 int catfhe_device_status(catfhe_ctx *ctx, int32_t *flags, int clear, void *stream);
 int catfhe_wait_selftest(catfhe_ctx *ctx, uint64_t limit_ns, void *stream);
 
