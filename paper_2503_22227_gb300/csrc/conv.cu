@@ -287,19 +287,22 @@ constexpr uint32_t kMask30 = (1u << 30) - 1;
 // Mixed-radix digits as 30-bit halves, and the centring decision (the
 // lexicographic comparison with the digits of (M-1)/2 runs from the least
 // significant digit up: the last differing digit decides).
-template <int KMAX>
+// EXACT: every plan of the launch has k = KMAX sources, so the source count
+// and the constants' row stride are compile-time constants.
+template <int KMAX, bool EXACT>
 __device__ __forceinline__ bool mixed_radix_split(const uint64_t (&r)[KMAX], uint32_t (&al)[KMAX],
                                                   uint32_t (&ah)[KMAX], const MontView &P) {
+    const uint32_t k = EXACT ? uint32_t(KMAX) : P.k;
     bool gt = false;
 #pragma unroll
     for (int j = 0; j < KMAX; j++) {
         al[j] = ah[j] = 0;
-        if (uint32_t(j) < P.k) {
+        if (uint32_t(j) < k) {
             Acc3 acc{0, 0, 0};
-            mac3(acc, uint32_t(r[j]) & kMask30, uint32_t(r[j] >> 30), P.C[size_t(j) * P.k + j]);
+            mac3(acc, uint32_t(r[j]) & kMask30, uint32_t(r[j] >> 30), P.C[size_t(j) * k + j]);
 #pragma unroll
             for (int i = 0; i < KMAX; i++)
-                if (i < j) mac3(acc, al[i], ah[i], P.C[size_t(i) * P.k + j]);
+                if (i < j) mac3(acc, al[i], ah[i], P.C[size_t(i) * k + j]);
             const uint64_t mj = P.smod[2 * j];
             const uint64_t aj = csub(redc(join3(acc), mj, P.smod[2 * j + 1]), mj);
             al[j] = uint32_t(aj) & kMask30;
@@ -311,15 +314,15 @@ __device__ __forceinline__ bool mixed_radix_split(const uint64_t (&r)[KMAX], uin
 }
 
 // Targets t and t+1 (two independent chains).
-template <int KMAX>
+template <int KMAX, bool EXACT>
 __device__ __forceinline__ void eval_split2(const uint32_t (&al)[KMAX], const uint32_t (&ah)[KMAX],
                                             bool gt, const MontView &P, uint32_t t, uint64_t &r0,
                                             uint64_t &r1) {
-    const uint32_t T = P.T;
+    const uint32_t T = P.T, k = EXACT ? uint32_t(KMAX) : P.k;
     Acc3 a0{0, 0, 0}, a1{0, 0, 0};
 #pragma unroll
     for (int i = 0; i < KMAX; i++) {
-        if (uint32_t(i) < P.k) {
+        if (uint32_t(i) < k) {
             mac3(a0, al[i], ah[i], P.Ct[size_t(i) * T + t]);
             mac3(a1, al[i], ah[i], P.Ct[size_t(i) * T + t + 1]);
         }
@@ -337,14 +340,15 @@ __device__ __forceinline__ void eval_split2(const uint32_t (&al)[KMAX], const ui
     }
 }
 
-template <int KMAX>
+template <int KMAX, bool EXACT>
 __device__ __forceinline__ uint64_t eval_split(const uint32_t (&al)[KMAX],
                                                const uint32_t (&ah)[KMAX], bool gt,
                                                const MontView &P, uint32_t t) {
+    const uint32_t k = EXACT ? uint32_t(KMAX) : P.k;
     Acc3 a{0, 0, 0};
 #pragma unroll
     for (int i = 0; i < KMAX; i++)
-        if (uint32_t(i) < P.k) mac3(a, al[i], ah[i], P.Ct[size_t(i) * P.T + t]);
+        if (uint32_t(i) < k) mac3(a, al[i], ah[i], P.Ct[size_t(i) * P.T + t]);
     if (gt) a.ll += P.Mneg[t];
     const uint64_t p = P.dmod[2 * t];
     const uint64_t r = redc(join3(a), p, P.dmod[2 * t + 1]);
@@ -361,7 +365,7 @@ __device__ __forceinline__ void load_sources(uint64_t (&a)[KMAX], uint32_t k,
     for (int i = 0; i < KMAX; i++) a[i] = uint32_t(i) < k ? s[src_off[i] * n + x] : 0;
 }
 
-template <int KMAX, bool MONT, bool SPLIT = false>
+template <int KMAX, bool MONT, bool SPLIT = false, bool EXACT = false>
 __global__ void __launch_bounds__(256, 4)
 k_conv(const PlanList plans, const uint64_t *__restrict__ src, size_t src_item, size_t src_plan,
        uint64_t *__restrict__ dst, size_t dst_item, size_t dst_plan, uint32_t log_n) {
@@ -377,17 +381,17 @@ k_conv(const PlanList plans, const uint64_t *__restrict__ src, size_t src_item, 
         for (size_t x = size_t(blockIdx.x) * blockDim.x + threadIdx.x; x < n;
              x += size_t(gridDim.x) * blockDim.x) {
             uint64_t r[KMAX];
-            load_sources<KMAX>(r, P.k, P.src_off, s, x, n);
+            load_sources<KMAX>(r, EXACT ? uint32_t(KMAX) : P.k, P.src_off, s, x, n);
             uint32_t al[KMAX], ah[KMAX];
-            const bool gt = mixed_radix_split<KMAX>(r, al, ah, P);
+            const bool gt = mixed_radix_split<KMAX, EXACT>(r, al, ah, P);
             uint32_t t = 0;
             for (; t + 1 < P.T; t += 2) {
                 uint64_t r0, r1;
-                eval_split2<KMAX>(al, ah, gt, P, t, r0, r1);
+                eval_split2<KMAX, EXACT>(al, ah, gt, P, t, r0, r1);
                 d[P.dst_off[t] * n + x] = r0;
                 d[P.dst_off[t + 1] * n + x] = r1;
             }
-            if (t < P.T) d[P.dst_off[t] * n + x] = eval_split<KMAX>(al, ah, gt, P, t);
+            if (t < P.T) d[P.dst_off[t] * n + x] = eval_split<KMAX, EXACT>(al, ah, gt, P, t);
         }
     } else if (MONT) {
         const MontView P = mont_view(splan);
@@ -490,12 +494,27 @@ int launch_conv(const Context &c, const PlanList &plans, const uint64_t *src, si
     const size_t sm = size_t(plans.words) * 8;
     if (plans.split) {
         if (plans.kmax > 8) return CATFHE_EINVAL;
-        if (plans.kmax <= 4)
+        if (plans.kmin == plans.kmax && plans.kmax <= 5) {
+            // one source count for every plan: exact instantiation (above 5
+            // sources the exact forms spill under the 64-register bound)
+            switch (plans.kmax) {
+#define EXACTK(K)                                                                              \
+    case K:                                                                                    \
+        k_conv<K, true, true, true><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, \
+                                                          dst_item, dst_plan, c.log_n);        \
+        break;
+                EXACTK(1) EXACTK(2) EXACTK(3) EXACTK(4) EXACTK(5)
+#undef EXACTK
+                default:
+                    return CATFHE_EINVAL;
+            }
+        } else if (plans.kmax <= 4) {
             k_conv<4, true, true><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst,
                                                         dst_item, dst_plan, c.log_n);
-        else
+        } else {
             k_conv<8, true, true><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst,
                                                         dst_item, dst_plan, c.log_n);
+        }
     } else if (plans.mont)
         run_conv<true>(pick_kmax(plans.kmax), grid, sm, s, plans, src, src_item, src_plan, dst,
                        dst_item, dst_plan, c.log_n);

@@ -109,6 +109,7 @@ struct PlanList {
     const uint64_t *p[64];
     uint32_t n;      // plans in the launch
     uint32_t kmax;   // largest source count among them
+    uint32_t kmin;   // smallest source count among them
     uint32_t words;  // largest packed size among them
     uint32_t mont;   // all plans use the Montgomery layout
     uint32_t split;  // ... with split weights

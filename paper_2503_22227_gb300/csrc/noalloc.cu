@@ -124,6 +124,7 @@ int op_rescale_noalloc_impl(Context &c, const uint64_t *a, uint64_t *out, uint32
     PlanList pl{};
     pl.n = 1;
     pl.kmax = 1;
+    pl.kmin = 1;
     pl.words = uint32_t(words);
     pl.mont = 1;
     pl.p[0] = plan;

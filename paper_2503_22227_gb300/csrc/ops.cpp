@@ -75,6 +75,8 @@ static int make_list(Context &c, const std::vector<std::pair<std::string, PlanSp
         if (r.mont != (pl.mont != 0) || r.split != (pl.split != 0)) return CATFHE_EINVAL;
         pl.p[i] = r.p;
         pl.kmax = std::max<uint32_t>(pl.kmax, uint32_t(sp.src_mod.size()));
+        pl.kmin = i == 0 ? uint32_t(sp.src_mod.size())
+                         : std::min<uint32_t>(pl.kmin, uint32_t(sp.src_mod.size()));
         pl.words = std::max(pl.words, r.words);
     }
     return CATFHE_OK;
