@@ -366,7 +366,7 @@ __device__ __forceinline__ void load_sources(uint64_t (&a)[KMAX], uint32_t k,
 }
 
 template <int KMAX, bool MONT, bool SPLIT = false, bool EXACT = false>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, (EXACT && KMAX > 5) ? 3 : 4)
 k_conv(const PlanList plans, const uint64_t *__restrict__ src, size_t src_item, size_t src_plan,
        uint64_t *__restrict__ dst, size_t dst_item, size_t dst_plan, uint32_t log_n) {
     extern __shared__ uint64_t splan[];
@@ -494,16 +494,16 @@ int launch_conv(const Context &c, const PlanList &plans, const uint64_t *src, si
     const size_t sm = size_t(plans.words) * 8;
     if (plans.split) {
         if (plans.kmax > 8) return CATFHE_EINVAL;
-        if (plans.kmin == plans.kmax && plans.kmax <= 5) {
+        if (plans.kmin == plans.kmax) {
             // one source count for every plan: exact instantiation (above 5
-            // sources the exact forms spill under the 64-register bound)
+            // sources it runs 3 CTAs per SM: under 64 registers it spills)
             switch (plans.kmax) {
 #define EXACTK(K)                                                                              \
     case K:                                                                                    \
         k_conv<K, true, true, true><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, \
                                                           dst_item, dst_plan, c.log_n);        \
         break;
-                EXACTK(1) EXACTK(2) EXACTK(3) EXACTK(4) EXACTK(5)
+                EXACTK(1) EXACTK(2) EXACTK(3) EXACTK(4) EXACTK(5) EXACTK(6) EXACTK(7) EXACTK(8)
 #undef EXACTK
                 default:
                     return CATFHE_EINVAL;
