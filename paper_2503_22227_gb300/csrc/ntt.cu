@@ -205,7 +205,7 @@ __device__ __forceinline__ void fwd_rows_body(uint64_t (&x)[1 << LOGE], uint64_t
 }
 
 template <int LOGR, int LOGE, bool EPI>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, EPI ? 3 : 4)
 k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__restrict__ mods,
                const ulonglong2 *__restrict__ tw, int log_n, const NttEpilogue epi) {
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CC = 256 / T;
@@ -229,6 +229,14 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
     uint64_t x[E];
 #pragma unroll
     for (int v = 0; v < E; v++) x[v] = base[tau + T * v];
+    // combine epilogue: its y words are loaded before the butterflies, so the
+    // loads overlap them (measured: 1648 -> 1613 us per batched step)
+    uint64_t yv[EPI ? E : 1];
+    if (EPI) {
+        const uint64_t *yp0 = epi.y + (size_t(g) * epi.y_stride + epi.y_off[r]) * N + size_t(h) * R;
+#pragma unroll
+        for (int v = 0; v < E; v++) yv[EPI ? v : 0] = yp0[tau + T * v];
+    }
     if (q < kWideBound) {
         // no conditional subtractions in either pass: words stay below
         // 4q + 2 log2(N) q <= 36q < 2^64, reduced once at the end
@@ -247,7 +255,6 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
     } else {
         // ModDown combine: out = (y - lift) * D^-1 (+ add), lift now in NTT form
         const size_t off = size_t(h) * R;
-        const uint64_t *yp = epi.y + (size_t(g) * epi.y_stride + epi.y_off[r]) * N + off;
         uint64_t *op = (epi.gathered ? epi.gout[g] : epi.out + size_t(g) * epi.out_stride * N) +
                        size_t(epi.out_off[r]) * N + off;
         const uint64_t *ap =
@@ -256,7 +263,7 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
 #pragma unroll
         for (int v = 0; v < E; v++) {
             const int u = tau + T * v;
-            uint64_t o = shoup(yp[u] + q - s[PAD(u)], dv, dvs, q);
+            uint64_t o = shoup(yv[EPI ? v : 0] + q - s[PAD(u)], dv, dvs, q);
             if (ap) o = add_mod(o, ap[u], q);
             op[u] = o;
         }
