@@ -490,7 +490,7 @@ int launch_conv(const Context &c, const PlanList &plans, const uint64_t *src, si
                 cudaStream_t s) {
     if (plans.n == 0 || items == 0) return CATFHE_OK;
     const size_t n = c.n;
-    dim3 grid(unsigned((n + 1023) / 1024), items, plans.n);
+    dim3 grid(unsigned((n + 255) / 256), items, plans.n);  // one coefficient per thread (fewer tail waves)
     const size_t sm = size_t(plans.words) * 8;
     if (plans.split) {
         if (plans.kmax > 8) return CATFHE_EINVAL;
