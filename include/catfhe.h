@@ -199,7 +199,10 @@ int catfhe_add(catfhe_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *
  * (BFV: exact round(t x / Q) of the tensor over Q u B), then hybrid key
  * switching of d2 with the relinearisation key: exact ModUp of each digit
  * to Q_l u P, inner product with the key, exact ModDown round(x / P)
- * (BGV: (x - d) / P with d = t [x t^-1]_P).  Output at `level`. */
+ * (BGV: (x - d) / P with d = t [x t^-1]_P).  Output at `level`.
+ * With count >= 4 and N >= 2^14 the ciphertexts run as two halves on two
+ * library streams forked from `stream` and joined back (results identical;
+ * this and catfhe_rotate enqueue under a process-wide lock). */
 int catfhe_mul_relin(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
                      const uint64_t *b, uint64_t *out, uint32_t level, uint32_t count,
                      void *ws, size_t ws_bytes, void *stream);

@@ -24,10 +24,10 @@ namespace catfhe {
 size_t ws_bytes(const Context &c, int op, uint32_t level, uint32_t count);
 int op_mul_relin(Context &c, const Keys &keys, const uint64_t *a, const uint64_t *b,
                  uint64_t *out, uint32_t level, uint32_t count, bool fused, void *ws,
-                 size_t ws_bytes_in, cudaStream_t s, const Gather *gth);
+                 size_t ws_bytes_in, cudaStream_t s, const Gather *gth, bool split);
 int op_rotate(Context &c, const Keys &keys, const uint64_t *a, uint64_t g, uint64_t *out,
               uint32_t level, uint32_t count, void *ws, size_t ws_bytes_in, cudaStream_t s,
-              const Gather *gth);
+              const Gather *gth, bool split);
 int op_rescale(Context &c, const uint64_t *a, uint64_t *out, uint32_t level, uint32_t count,
                void *ws, size_t ws_bytes_in, cudaStream_t s);
 int op_add(Context &c, const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t level,
@@ -237,11 +237,11 @@ int run_one(const catfhe_op &o, void *ws, size_t ws_bytes_in, cudaStream_t s) {
     Context &c = o.ctx->c;
     switch (o.op) {
         case CATFHE_OP_MUL_RELIN:
-            return op_mul_relin(c, *o.keys->k, o.a, o.b, o.out, o.level, o.count, false, ws, ws_bytes_in, s, nullptr);
+            return op_mul_relin(c, *o.keys->k, o.a, o.b, o.out, o.level, o.count, false, ws, ws_bytes_in, s, nullptr, false);
         case CATFHE_OP_MUL_RELIN_RESCALE:
-            return op_mul_relin(c, *o.keys->k, o.a, o.b, o.out, o.level, o.count, true, ws, ws_bytes_in, s, nullptr);
+            return op_mul_relin(c, *o.keys->k, o.a, o.b, o.out, o.level, o.count, true, ws, ws_bytes_in, s, nullptr, false);
         case CATFHE_OP_ROTATE:
-            return op_rotate(c, *o.keys->k, o.a, o.arg, o.out, o.level, o.count, ws, ws_bytes_in, s, nullptr);
+            return op_rotate(c, *o.keys->k, o.a, o.arg, o.out, o.level, o.count, ws, ws_bytes_in, s, nullptr, false);
         case CATFHE_OP_RESCALE:
             return op_rescale(c, o.a, o.out, o.level, o.count, ws, ws_bytes_in, s);
         case CATFHE_OP_ADD:
@@ -277,9 +277,9 @@ int run_unit(const catfhe_op *ops, const Unit &u, void *ws, size_t ws_bytes_in, 
         case CATFHE_OP_MUL_RELIN:
         case CATFHE_OP_MUL_RELIN_RESCALE:
             return op_mul_relin(c, *o.keys->k, o.a, o.b, o.out, o.level, g.n,
-                                o.op == CATFHE_OP_MUL_RELIN_RESCALE, ws, ws_bytes_in, s, &g);
+                                o.op == CATFHE_OP_MUL_RELIN_RESCALE, ws, ws_bytes_in, s, &g, false);
         case CATFHE_OP_ROTATE:
-            return op_rotate(c, *o.keys->k, o.a, o.arg, o.out, o.level, g.n, ws, ws_bytes_in, s, &g);
+            return op_rotate(c, *o.keys->k, o.a, o.arg, o.out, o.level, g.n, ws, ws_bytes_in, s, &g, false);
         default:
             return CATFHE_EINVAL;
     }

@@ -13,10 +13,10 @@ size_t ws_bytes(const Context &c, int op, uint32_t level, uint32_t count);
 int op_mul_relin(Context &c, const Keys &keys, const uint64_t *a, const uint64_t *b,
                  uint64_t *out, uint32_t level, uint32_t count, bool fused, void *ws,
                  size_t ws_bytes_in, cudaStream_t s,
-                 const Gather *gth = nullptr);
+                 const Gather *gth = nullptr, bool split = false);
 int op_rotate(Context &c, const Keys &keys, const uint64_t *a, uint64_t g, uint64_t *out,
               uint32_t level, uint32_t count, void *ws, size_t ws_bytes_in, cudaStream_t s,
-              const Gather *gth = nullptr);
+              const Gather *gth = nullptr, bool split = false);
 int op_plain_import(Context &c, const int64_t *coeffs, uint32_t level, uint64_t *pt,
                     cudaStream_t s);
 int op_encode_ckks(Context &c, const double *slots, double scale, uint32_t level, uint64_t *pt,
@@ -235,21 +235,24 @@ int catfhe_mul_relin(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a
                      const uint64_t *b, uint64_t *out, uint32_t level, uint32_t count,
                      void *ws, size_t ws_bytes, void *stream) {
     if (!keys_ok(ctx, keys) || !a || !b || !out) return CATFHE_EINVAL;
-    return op_mul_relin(ctx->c, *keys->k, a, b, out, level, count, false, ws, ws_bytes, S(stream));
+    return op_mul_relin(ctx->c, *keys->k, a, b, out, level, count, false, ws, ws_bytes, S(stream),
+                        nullptr, true);
 }
 
 int catfhe_mul_relin_rescale(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
                              const uint64_t *b, uint64_t *out, uint32_t level, uint32_t count,
                              void *ws, size_t ws_bytes, void *stream) {
     if (!keys_ok(ctx, keys) || !a || !b || !out) return CATFHE_EINVAL;
-    return op_mul_relin(ctx->c, *keys->k, a, b, out, level, count, true, ws, ws_bytes, S(stream));
+    return op_mul_relin(ctx->c, *keys->k, a, b, out, level, count, true, ws, ws_bytes, S(stream),
+                        nullptr, true);
 }
 
 int catfhe_rotate(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
                   uint64_t galois_elt, uint64_t *out, uint32_t level, uint32_t count, void *ws,
                   size_t ws_bytes, void *stream) {
     if (!keys_ok(ctx, keys) || !a || !out) return CATFHE_EINVAL;
-    return op_rotate(ctx->c, *keys->k, a, galois_elt, out, level, count, ws, ws_bytes, S(stream));
+    return op_rotate(ctx->c, *keys->k, a, galois_elt, out, level, count, ws, ws_bytes, S(stream),
+                     nullptr, true);
 }
 
 int catfhe_device_status(catfhe_ctx *ctx, int32_t *flags, int clear, void *stream) {
