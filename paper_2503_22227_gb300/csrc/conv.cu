@@ -30,6 +30,7 @@
 // One thread handles one coefficient of one item; the packed plan (a few
 // KB) sits in shared memory and every thread reads the same words
 // (broadcast).
+#include "launch.cuh"
 #include "modarith.cuh"
 
 namespace catfhe {
@@ -369,6 +370,7 @@ template <int KMAX, bool MONT, bool SPLIT = false, bool EXACT = false>
 __global__ void __launch_bounds__(256, (EXACT && KMAX > 5) ? 3 : 4)
 k_conv(const PlanList plans, const uint64_t *__restrict__ src, size_t src_item, size_t src_plan,
        uint64_t *__restrict__ dst, size_t dst_item, size_t dst_plan, uint32_t log_n) {
+    grid_dep_wait();
     extern __shared__ uint64_t splan[];
     const uint64_t *gp = plans.p[blockIdx.z];
     copy_plan(splan, gp, uint32_t(plan_words(gp[0])));
@@ -478,10 +480,10 @@ static void run_conv(int kmax, dim3 grid, size_t sm, cudaStream_t s, const PlanL
                      const uint64_t *src, size_t src_item, size_t src_plan, uint64_t *dst,
                      size_t dst_item, size_t dst_plan, uint32_t log_n) {
     switch (kmax) {
-        case 4: k_conv<4, MONT><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, dst_item, dst_plan, log_n); break;
-        case 8: k_conv<8, MONT><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, dst_item, dst_plan, log_n); break;
-        case 16: k_conv<16, MONT><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, dst_item, dst_plan, log_n); break;
-        default: k_conv<32, MONT><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, dst_item, dst_plan, log_n); break;
+        case 4: launch_pdl(k_conv<4, MONT>, grid, dim3(256), sm, s, plans, src, src_item, src_plan, dst, dst_item, dst_plan, log_n); break;
+        case 8: launch_pdl(k_conv<8, MONT>, grid, dim3(256), sm, s, plans, src, src_item, src_plan, dst, dst_item, dst_plan, log_n); break;
+        case 16: launch_pdl(k_conv<16, MONT>, grid, dim3(256), sm, s, plans, src, src_item, src_plan, dst, dst_item, dst_plan, log_n); break;
+        default: launch_pdl(k_conv<32, MONT>, grid, dim3(256), sm, s, plans, src, src_item, src_plan, dst, dst_item, dst_plan, log_n); break;
     }
 }
 
@@ -500,7 +502,7 @@ int launch_conv(const Context &c, const PlanList &plans, const uint64_t *src, si
             switch (plans.kmax) {
 #define EXACTK(K)                                                                              \
     case K:                                                                                    \
-        k_conv<K, true, true, true><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst, \
+        launch_pdl(k_conv<K, true, true, true>, grid, dim3(256), sm, s, plans, src, src_item, src_plan, dst, \
                                                           dst_item, dst_plan, c.log_n);        \
         break;
                 EXACTK(1) EXACTK(2) EXACTK(3) EXACTK(4) EXACTK(5) EXACTK(6) EXACTK(7) EXACTK(8)
@@ -509,10 +511,10 @@ int launch_conv(const Context &c, const PlanList &plans, const uint64_t *src, si
                     return CATFHE_EINVAL;
             }
         } else if (plans.kmax <= 4) {
-            k_conv<4, true, true><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst,
+            launch_pdl(k_conv<4, true, true>, grid, dim3(256), sm, s, plans, src, src_item, src_plan, dst,
                                                         dst_item, dst_plan, c.log_n);
         } else {
-            k_conv<8, true, true><<<grid, 256, sm, s>>>(plans, src, src_item, src_plan, dst,
+            launch_pdl(k_conv<8, true, true>, grid, dim3(256), sm, s, plans, src, src_item, src_plan, dst,
                                                         dst_item, dst_plan, c.log_n);
         }
     } else if (plans.mont)

@@ -7,6 +7,7 @@
 // consecutive threads on consecutive words, grids sized by the data (a whole
 // batch of ciphertexts per launch).
 #include "bulk.cuh"
+#include "launch.cuh"
 #include "modarith.cuh"
 
 namespace catfhe {
@@ -32,6 +33,7 @@ __device__ __forceinline__ void st2(uint64_t *p, uint64_t a, uint64_t b) {
 // Two adjacent coefficients per thread (16-byte loads and stores).
 __global__ void __launch_bounds__(256)
 k_tensor(const TensorArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
+    grid_dep_wait();
     const size_t n = size_t(1) << log_n;
     const size_t x = 2 * (size_t(blockIdx.x) * blockDim.x + threadIdx.x);
     const uint32_t i = blockIdx.y, item = blockIdx.z;
@@ -53,7 +55,7 @@ k_tensor(const TensorArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
 }
 
 int launch_tensor(const Context &c, const TensorArgs &a, uint32_t count, cudaStream_t s) {
-    k_tensor<<<coeff_grid(c.n / 2, a.limbs, count), 256, 0, s>>>(a, c.d_mods, c.log_n);
+    launch_pdl(k_tensor, coeff_grid(c.n / 2, a.limbs, count), dim3(256), 0, s, a, c.d_mods, c.log_n);
     return ok();
 }
 
@@ -115,6 +117,7 @@ __device__ __forceinline__ void ip_body(const IpArgs &A, const DevMod &m, uint32
 template <int BETA>
 __global__ void __launch_bounds__(256)
 k_ip(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
+    grid_dep_wait();
     const size_t n = size_t(1) << log_n;
     const uint32_t item = blockIdx.x, i = blockIdx.z;
     const size_t x = 2 * (size_t(blockIdx.y) * blockDim.x + threadIdx.x);
@@ -127,6 +130,7 @@ k_ip(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
 // so registers stay bounded.
 __global__ void __launch_bounds__(256)
 k_ip_stream(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
+    grid_dep_wait();
     const size_t n = size_t(1) << log_n;
     const uint32_t item = blockIdx.x, i = blockIdx.z;
     const size_t x = 2 * (size_t(blockIdx.y) * blockDim.x + threadIdx.x);
@@ -178,6 +182,7 @@ constexpr uint32_t kIpTile = 512;
 template <int BETA>
 __global__ void __launch_bounds__(256)
 k_ip_bulk(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n, uint32_t count) {
+    grid_dep_wait();
     extern __shared__ __align__(128) uint64_t sm[];
     __shared__ __align__(8) uint64_t bars[3];  // buffer 0, buffer 1, keys
     const size_t n = size_t(1) << log_n;
@@ -312,7 +317,7 @@ int launch_ip(const Context &c, const IpArgs &a, uint32_t count, cudaStream_t s)
         if (cudaFuncSetAttribute(k_ip_bulk<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                  int(smb)) != cudaSuccess)                                       \
             return CATFHE_ECUDA;                                                                 \
-        k_ip_bulk<B><<<g, 256, smb, s>>>(a, c.d_mods, c.log_n, count);                           \
+        launch_pdl(k_ip_bulk<B>, g, dim3(256), smb, s, a, c.d_mods, c.log_n, count);             \
         break;                                                                                   \
     }
             IPB(1) IPB(2) IPB(3) IPB(4)
@@ -327,15 +332,15 @@ int launch_ip(const Context &c, const IpArgs &a, uint32_t count, cudaStream_t s)
 static int launch_ip_regs(const Context &c, const IpArgs &a, uint32_t count, cudaStream_t s) {
     const dim3 g(count, unsigned((c.n / 2 + 255) / 256), a.M);
     switch (a.beta) {
-        case 1: k_ip<1><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n); break;
-        case 2: k_ip<2><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n); break;
-        case 3: k_ip<3><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n); break;
-        case 4: k_ip<4><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n); break;
+        case 1: launch_pdl(k_ip<1>, g, dim3(256), 0, s, a, c.d_mods, c.log_n); break;
+        case 2: launch_pdl(k_ip<2>, g, dim3(256), 0, s, a, c.d_mods, c.log_n); break;
+        case 3: launch_pdl(k_ip<3>, g, dim3(256), 0, s, a, c.d_mods, c.log_n); break;
+        case 4: launch_pdl(k_ip<4>, g, dim3(256), 0, s, a, c.d_mods, c.log_n); break;
         default:
             if (a.beta <= 8)
-                k_ip<8><<<g, 256, 0, s>>>(a, c.d_mods, c.log_n);
+                launch_pdl(k_ip<8>, g, dim3(256), 0, s, a, c.d_mods, c.log_n);
             else
-                k_ip_stream<<<g, 256, 0, s>>>(a, c.d_mods, c.log_n);
+                launch_pdl(k_ip_stream, g, dim3(256), 0, s, a, c.d_mods, c.log_n);
     }
     return ok();
 }
@@ -369,6 +374,7 @@ int launch_combine(const Context &c, const CombineArgs &a, uint32_t count, cudaS
 __global__ void __launch_bounds__(256)
 k_automorph_ntt(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, uint64_t g,
                 uint32_t log_n) {
+    grid_dep_wait();
     const size_t n = size_t(1) << log_n;
     const size_t k = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -382,13 +388,15 @@ k_automorph_ntt(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, uin
 
 int launch_automorph_ntt(const Context &c, const uint64_t *in, uint64_t *out, uint32_t limbs_total,
                          uint64_t g, cudaStream_t s) {
-    k_automorph_ntt<<<coeff_grid(c.n, limbs_total), 256, 0, s>>>(in, out, g % (2 * c.n), c.log_n);
+    launch_pdl(k_automorph_ntt, coeff_grid(c.n, limbs_total), dim3(256), 0, s, in, out,
+               uint64_t(g % (2 * c.n)), uint32_t(c.log_n));
     return ok();
 }
 
 __global__ void __launch_bounds__(256)
 k_automorph_ntt_map(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, const LimbMap map,
                     uint64_t g, uint32_t log_n) {
+    grid_dep_wait();
     const size_t n = size_t(1) << log_n;
     const size_t k = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -404,8 +412,8 @@ k_automorph_ntt_map(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
 int launch_automorph_ntt_map(const Context &c, const uint64_t *in, uint64_t *out,
                              const LimbMap &map, uint32_t limbs_total, uint64_t g, cudaStream_t s) {
     if (limbs_total == 0) return CATFHE_OK;
-    k_automorph_ntt_map<<<coeff_grid(c.n, limbs_total), 256, 0, s>>>(in, out, map, g % (2 * c.n),
-                                                                      c.log_n);
+    launch_pdl(k_automorph_ntt_map, coeff_grid(c.n, limbs_total), dim3(256), 0, s, in, out, map,
+               uint64_t(g % (2 * c.n)), uint32_t(c.log_n));
     return ok();
 }
 

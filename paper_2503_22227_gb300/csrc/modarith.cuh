@@ -17,6 +17,10 @@ __device__ __forceinline__ uint64_t mulhi(uint64_t a, uint64_t b) { return __umu
 
 __device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t q) { return x >= q ? x - q : x; }
 
+// Waits for the previous kernel on the stream (launches with programmatic
+// dependent launch, launch.cuh); a no-op for ordinary launches.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q) {
     return csub(a + b, q);
 }

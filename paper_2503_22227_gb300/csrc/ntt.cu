@@ -20,6 +20,7 @@
 // every limb of the batch (blockIdx.y), so one launch covers a whole batch
 // of ciphertexts: no per-modulus kernels or streams (the paper's kernel
 // segmentation, Sec. 3.1.4, is replaced by batching).
+#include "launch.cuh"
 #include "modarith.cuh"
 
 namespace catfhe {
@@ -139,6 +140,7 @@ template <int LOGR, int LOGE>
 __global__ void __launch_bounds__(256)
 k_ntt_fwd_cols(const uint64_t *src, uint64_t *dst, const LimbMap map,
                const DevMod *__restrict__ mods, const ulonglong2 *__restrict__ tw, int log_n) {
+    grid_dep_wait();
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CW = 256 / T;
     __shared__ uint64_t sm[R * CW];
     uint32_t g, r;
@@ -208,6 +210,7 @@ template <int LOGR, int LOGE, bool EPI>
 __global__ void __launch_bounds__(256, EPI ? 3 : 4)
 k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__restrict__ mods,
                const ulonglong2 *__restrict__ tw, int log_n, const NttEpilogue epi) {
+    grid_dep_wait();
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CC = 256 / T;
     constexpr int RP = R + R / E;
     __shared__ uint64_t sm[CC * RP];
@@ -277,6 +280,7 @@ template <int LOGR, int LOGE>
 __global__ void __launch_bounds__(256)
 k_ntt_inv_rows(const uint64_t *src, uint64_t *dst, const LimbMap map,
                const DevMod *__restrict__ mods, const ulonglong2 *__restrict__ tw, int log_n) {
+    grid_dep_wait();
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CC = 256 / T;
     constexpr int RP = R + R / E;
     __shared__ uint64_t sm[CC * RP];
@@ -338,6 +342,7 @@ template <int LOGR, int LOGE>
 __global__ void __launch_bounds__(256)
 k_ntt_inv_cols(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__restrict__ mods,
                const ulonglong2 *__restrict__ tw, int log_n) {
+    grid_dep_wait();
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CW = 256 / T;
     __shared__ uint64_t sm[R * CW];
     uint32_t g, r;
@@ -403,13 +408,14 @@ static int run_fwd(const Context &c, const uint64_t *src, uint64_t *dst, const L
                    uint32_t n_limbs, cudaStream_t s, const NttEpilogue *epi = nullptr) {
     const size_t N = c.n;
     dim3 g1(unsigned((N >> R1) / (256 / ((1 << R1) >> E1))), n_limbs);
-    k_ntt_fwd_cols<R1, E1><<<g1, 256, 0, s>>>(src, dst, map, c.d_mods, c.d_twf, c.log_n);
+    launch_pdl(k_ntt_fwd_cols<R1, E1>, g1, dim3(256), 0, s, src, dst, map, c.d_mods, c.d_twf, c.log_n);
     dim3 g2(unsigned((N >> R2) / (256 / ((1 << R2) >> E2))), n_limbs);
     if (epi)
-        k_ntt_fwd_rows<R2, E2, true><<<g2, 256, 0, s>>>(dst, map, c.d_mods, c.d_twf, c.log_n, *epi);
+        launch_pdl(k_ntt_fwd_rows<R2, E2, true>, g2, dim3(256), 0, s, dst, map, c.d_mods, c.d_twf,
+                   c.log_n, *epi);
     else
-        k_ntt_fwd_rows<R2, E2, false><<<g2, 256, 0, s>>>(dst, map, c.d_mods, c.d_twf, c.log_n,
-                                                         NttEpilogue{});
+        launch_pdl(k_ntt_fwd_rows<R2, E2, false>, g2, dim3(256), 0, s, dst, map, c.d_mods, c.d_twf,
+                   c.log_n, NttEpilogue{});
     note_launches(2);
     return cudaGetLastError() == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
 }
@@ -419,9 +425,9 @@ static int run_inv(const Context &c, const uint64_t *src, uint64_t *dst, const L
                    uint32_t n_limbs, cudaStream_t s) {
     const size_t N = c.n;
     dim3 g2(unsigned((N >> R2) / (256 / ((1 << R2) >> E2))), n_limbs);
-    k_ntt_inv_rows<R2, E2><<<g2, 256, 0, s>>>(src, dst, map, c.d_mods, c.d_twi, c.log_n);
+    launch_pdl(k_ntt_inv_rows<R2, E2>, g2, dim3(256), 0, s, src, dst, map, c.d_mods, c.d_twi, c.log_n);
     dim3 g1(unsigned((N >> R1) / (256 / ((1 << R1) >> E1))), n_limbs);
-    k_ntt_inv_cols<R1, E1><<<g1, 256, 0, s>>>(dst, map, c.d_mods, c.d_twi, c.log_n);
+    launch_pdl(k_ntt_inv_cols<R1, E1>, g1, dim3(256), 0, s, dst, map, c.d_mods, c.d_twi, c.log_n);
     note_launches(2);
     return cudaGetLastError() == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
 }
