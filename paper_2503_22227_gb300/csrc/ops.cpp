@@ -361,9 +361,11 @@ size_t ws_bytes(const Context &c, int op, uint32_t level, uint32_t count) {
             b.off = ks_ws(c, count, int(level), true);
             break;
         case CATFHE_OP_ROTATE_HOISTED: {
-            ks_layout(c, b, k, count, int(level), false);
+            // two per-rotation buffer sets (rotations alternate over two
+            // streams), then the shared lifted digits
+            b.off = 2 * ks_bytes(c, count, int(level), false);
             const int M = int(level) + c.K, beta = (int(level) + c.alpha - 1) / c.alpha;
-            b.take<uint64_t>(size_t(count) * beta * M * n);  // the shared lifted digits
+            b.take<uint64_t>(size_t(count) * beta * M * n);
             break;
         }
         case CATFHE_OP_RESCALE:
@@ -750,8 +752,12 @@ int op_rotate_hoisted(Context &c, const Keys &keys, const uint64_t *a, const uin
     char *base;
     TRY(get_ws(c, ws, ws_bytes_in, ws_bytes(c, CATFHE_OP_ROTATE_HOISTED, level, count), &base));
     Bump bump{base};
-    KsBufs k{};
-    ks_layout(c, bump, k, count, int(level), false);
+    KsBufs ks[2];
+    ks_layout(c, bump, ks[0], count, int(level), false);
+    bump.off = ks_bytes(c, count, int(level), false);
+    ks_layout(c, bump, ks[1], count, int(level), false);
+    bump.off = 2 * ks_bytes(c, count, int(level), false);
+    KsBufs &k = ks[0];
     const size_t n = c.n;
     const int lvl = int(level), M = lvl + c.K, beta = (lvl + c.alpha - 1) / c.alpha;
     uint64_t *ext0 = bump.take<uint64_t>(size_t(count) * beta * M * n);
@@ -785,13 +791,30 @@ int op_rotate_hoisted(Context &c, const Keys &keys, const uint64_t *a, const uin
     me.src_stride = me.dst_stride = uint32_t(beta * M);
     LimbMap m0 = m1;  // a0 -> d0
     for (int i = 0; i < lvl; i++) m0.src_off[i] = uint16_t(i);
-    for (uint32_t r = 0; r < n_rot; r++) {
-        TRY(launch_automorph_ntt_map(c, a, k.d0, m0, uint32_t(lvl) * count, gv[r], s));
-        TRY(launch_automorph_ntt_map(c, a, k.d2, m1, uint32_t(lvl) * count, gv[r], s));
-        TRY(launch_automorph_ntt_map(c, ext0, k.ext, me, e * count, gv[r], s));
-        TRY(inner_product(c, k.ext, k.d2, gk[r], k.d0, nullptr, k.y, count, lvl, s));
-        TRY(moddown(c, k.y, k.lift, out + size_t(r) * count * 2 * lvl * n, nullptr, count, lvl,
-                    false, s));
+    auto one = [&](uint32_t r, KsBufs &kb, cudaStream_t st) -> int {
+        TRY(launch_automorph_ntt_map(c, a, kb.d0, m0, uint32_t(lvl) * count, gv[r], st));
+        TRY(launch_automorph_ntt_map(c, a, kb.d2, m1, uint32_t(lvl) * count, gv[r], st));
+        TRY(launch_automorph_ntt_map(c, ext0, kb.ext, me, e * count, gv[r], st));
+        TRY(inner_product(c, kb.ext, kb.d2, gk[r], kb.d0, nullptr, kb.y, count, lvl, st));
+        return moddown(c, kb.y, kb.lift, out + size_t(r) * count * 2 * lvl * n, nullptr, count,
+                       lvl, false, st);
+    };
+    if (n_rot < 2 || c.log_n < 14) {
+        for (uint32_t r = 0; r < n_rot; r++) TRY(one(r, k, s));
+        return CATFHE_OK;
+    }
+    // rotations alternate over the two split streams, each with its own
+    // buffer set (in order on its stream), after the shared ModUp on s
+    std::lock_guard<std::mutex> lock(g_split_mu);
+    SplitPool *sp;
+    TRY(split_pool(&sp));
+    if (cudaEventRecord(sp->fork, s) != cudaSuccess) return CATFHE_ECUDA;
+    for (int h = 0; h < 2; h++)
+        if (cudaStreamWaitEvent(sp->st[h], sp->fork, 0) != cudaSuccess) return CATFHE_ECUDA;
+    for (uint32_t r = 0; r < n_rot; r++) TRY(one(r, ks[r & 1], sp->st[r & 1]));
+    for (int h = 0; h < 2; h++) {
+        if (cudaEventRecord(sp->join[h], sp->st[h]) != cudaSuccess) return CATFHE_ECUDA;
+        if (cudaStreamWaitEvent(s, sp->join[h], 0) != cudaSuccess) return CATFHE_ECUDA;
     }
     return CATFHE_OK;
 }

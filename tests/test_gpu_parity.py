@@ -517,3 +517,30 @@ def test_zero_count_is_a_noop(ckks12):
     assert rcs == [0] * len(rcs)
     torch.cuda.synchronize()
     assert bool((out == 7).all())
+
+
+def test_split_and_alternating_paths_equal_single_calls():
+    """N = 2^14: key switching on 5 ciphertexts runs as halves of 3 and 2 on
+    two streams, and hoisted rotations alternate over two streams; every
+    output must equal the single-ciphertext (unsplit) call."""
+    p = W.Preset("ckks_n14_small", W.CKKS, 14, (50,) * 6, (60, 60), 3, log_n_max=14)
+    ctx = api.Context(p)
+    keys = ctx.keygen(W.seed_for("split-keys"))
+    gs = [ctx.galois_elt(r) for r in (1, 2, -5)] + [2 * p.n - 1]
+    for g in gs:
+        keys.gen_galois(g)
+    seed = W.seed_for("split-in")
+    a = torch.cat([ctx.ct_uniform(seed, 2 * i, p.L) for i in range(5)])
+    b = torch.cat([ctx.ct_uniform(seed, 2 * i + 1, p.L) for i in range(5)])
+    for fused in (False, True):
+        whole = ctx.mul_relin_rescale(keys, a, b) if fused else ctx.mul_relin(keys, a, b)
+        for i in range(5):
+            one = (ctx.mul_relin_rescale(keys, a[i:i + 1], b[i:i + 1]) if fused
+                   else ctx.mul_relin(keys, a[i:i + 1], b[i:i + 1]))
+            assert torch.equal(whole[i:i + 1], one), (fused, i)
+    rot = ctx.rotate(keys, a, gs[0])
+    for i in range(5):
+        assert torch.equal(rot[i:i + 1], ctx.rotate(keys, a[i:i + 1], gs[0])), i
+    hoisted = ctx.rotate_hoisted(keys, a[:2], gs)
+    for r, g in enumerate(gs):
+        assert torch.equal(hoisted[r], ctx.rotate(keys, a[:2], g)), g
