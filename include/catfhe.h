@@ -350,14 +350,18 @@ int catfhe_device_status(catfhe_ctx *ctx, int32_t *flags, int clear, void *strea
 int catfhe_wait_selftest(catfhe_ctx *ctx, uint64_t limit_ns, void *stream);
 
 /* Diagnostics.  catfhe_measure_int_peak times register-resident loops of
- * independent 64-bit Shoup products by a constant and of full NTT
- * butterflies (Shoup product + modular add + modular subtract) on the
- * current device, filling the whole GPU; it reports the best of five
- * launches in operations per second (either pointer may be NULL) and
- * synchronises `stream`.  These are the integer-pipe ceilings the hot path
- * is measured against.  catfhe_kernel_launches returns how many kernels
- * the library has launched since it was loaded. */
-int catfhe_measure_int_peak(double *modmul_per_s, double *butterfly_per_s, void *stream);
+ * independent 64-bit Shoup products by a constant (fully reduced) and of
+ * the forward NTT's butterflies exactly as the transform runs them: for
+ * primes of 57 bits or more (`butterfly_per_s`: lazy product, one
+ * conditional subtraction, add, subtract) and for smaller primes
+ * (`butterfly_wide_per_s`: no conditional subtraction).  The loops fill the
+ * whole GPU; each result is the best of five launches in operations per
+ * second (any pointer may be NULL); `stream` is synchronised.  These are
+ * the integer-pipe ceilings the hot path is measured against.
+ * catfhe_kernel_launches returns how many kernels the library has launched
+ * since it was loaded. */
+int catfhe_measure_int_peak(double *modmul_per_s, double *butterfly_per_s,
+                            double *butterfly_wide_per_s, void *stream);
 uint64_t catfhe_kernel_launches(void);
 
 /* ---- Uneven batches (many independent operations in one submission) ----

@@ -117,7 +117,7 @@ def load(path: str = LIB_PATH):
             "catfhe_decrypt": (ctypes.c_int, [vp, vp, vp, u32, u64, vp, vp, sz, vp]),
             "catfhe_ntt": (ctypes.c_int, [vp, vp, u32, u32, ctypes.c_int, vp]),
             "catfhe_workspace_bytes": (sz, [vp, ctypes.c_int, u32, u32]),
-            "catfhe_measure_int_peak": (ctypes.c_int, [vp, vp, vp]),
+            "catfhe_measure_int_peak": (ctypes.c_int, [vp, vp, vp, vp]),
             "catfhe_kernel_launches": (u64, []),
             "catfhe_rescale_noalloc": (ctypes.c_int, [vp, vp, vp, u32, u32, vp]),
             "catfhe_batch_workspace_bytes": (sz, [vp, u32, u32]),
@@ -470,12 +470,14 @@ class Context:
         return limbs
 
 
-def measure_int_peak() -> tuple[float, float]:
-    """(Shoup modmul/s, NTT butterfly/s) ceilings of the current device."""
-    mm, bf = ctypes.c_double(), ctypes.c_double()
-    _check(load().catfhe_measure_int_peak(ctypes.byref(mm), ctypes.byref(bf), _stream()),
+def measure_int_peak() -> tuple[float, float, float]:
+    """(Shoup modmul/s, forward butterfly/s for primes of 57 bits or more,
+    forward butterfly/s for smaller primes) ceilings of the current device."""
+    mm, bf, bw = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().catfhe_measure_int_peak(ctypes.byref(mm), ctypes.byref(bf), ctypes.byref(bw),
+                                          _stream()),
            "catfhe_measure_int_peak")
-    return mm.value, bf.value
+    return mm.value, bf.value, bw.value
 
 
 def kernel_launches() -> int:

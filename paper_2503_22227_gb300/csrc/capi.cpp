@@ -57,7 +57,8 @@ int op_export(Context &c, const uint64_t *ct, uint32_t level, uint32_t count, in
               bool sync, uint64_t *host, void *ws, size_t ws_bytes_in, cudaStream_t s);
 int op_decrypt(Context &c, const Keys &k, const uint64_t *ct, uint32_t level, uint64_t factor,
                int64_t *msg, void *ws, size_t ws_bytes_in, cudaStream_t s);
-int measure_int_peak(double *modmul_per_s, double *bfly_per_s, cudaStream_t s);
+int measure_int_peak(double *modmul_per_s, double *bfly_per_s, double *bfly_wide_per_s,
+                     cudaStream_t s);
 int op_rescale_noalloc_impl(Context &c, const uint64_t *a, uint64_t *out, uint32_t level,
                             uint32_t count, cudaStream_t s);
 }  // namespace catfhe
@@ -337,8 +338,9 @@ int catfhe_ntt(catfhe_ctx *ctx, uint64_t *limbs, uint32_t level, uint32_t count,
     return op_ntt(ctx->c, limbs, level, count, inverse, S(stream));
 }
 
-int catfhe_measure_int_peak(double *modmul_per_s, double *butterfly_per_s, void *stream) {
-    return measure_int_peak(modmul_per_s, butterfly_per_s, S(stream));
+int catfhe_measure_int_peak(double *modmul_per_s, double *butterfly_per_s,
+                            double *butterfly_wide_per_s, void *stream) {
+    return measure_int_peak(modmul_per_s, butterfly_per_s, butterfly_wide_per_s, S(stream));
 }
 
 uint64_t catfhe_kernel_launches(void) { return launches_total(); }

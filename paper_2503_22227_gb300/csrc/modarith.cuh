@@ -35,6 +35,37 @@ __device__ __forceinline__ uint64_t shoup_lazy(uint64_t a, uint64_t w, uint64_t 
     return a * w + mulhi(a, ws) * (0 - q);
 }
 
+// floor(a b / 2^64) - e with e in {0, 1, 2}.  With a = a1 2^32 + a0 and
+// b = b1 2^32 + b0, a b / 2^64 = a1 b1 + hi(a1 b0) + hi(a0 b1) + R / 2^64
+// where R = (lo(a1 b0) + lo(a0 b1)) 2^32 + a0 b0 < 3 * 2^64; R is dropped.
+// Two 32-bit high products and one widening multiply-add, against the
+// exact high product's four partial products and their carries.
+__device__ __forceinline__ uint64_t mulhi_approx(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("{\n\t"
+        ".reg .u32 a0, a1, b0, b1, h1, h2, s, c;\n\t"
+        ".reg .u64 t;\n\t"
+        "mov.b64 {a0, a1}, %1;\n\t"
+        "mov.b64 {b0, b1}, %2;\n\t"
+        "mul.hi.u32 h1, a1, b0;\n\t"
+        "mul.hi.u32 h2, a0, b1;\n\t"
+        "add.cc.u32 s, h1, h2;\n\t"
+        "addc.u32 c, 0, 0;\n\t"
+        "mov.b64 t, {s, c};\n\t"
+        "mad.wide.u32 %0, a1, b1, t;\n\t"
+        "}"
+        : "=l"(r)
+        : "l"(a), "l"(b));
+    return r;
+}
+
+// a*w mod q in [0, 4q); any 64-bit a, w < q, ws = floor(w 2^64 / q).  The
+// quotient estimate is at most 2 below Shoup's, whose remainder is in
+// [0, 2q); the subtraction is exact modulo 2^64 since the result is < 2^64.
+__device__ __forceinline__ uint64_t shoup_lazy4(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
+    return a * w + mulhi_approx(a, ws) * (0 - q);
+}
+
 __device__ __forceinline__ uint64_t shoup(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
     return csub(shoup_lazy(a, w, ws, q), q);
 }

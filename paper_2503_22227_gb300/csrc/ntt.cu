@@ -20,60 +20,21 @@
 // every limb of the batch (blockIdx.y), so one launch covers a whole batch
 // of ciphertexts: no per-modulus kernels or streams (the paper's kernel
 // segmentation, Sec. 3.1.4, is replaced by batching).
+#include "butterfly.cuh"
 #include "launch.cuh"
 #include "modarith.cuh"
 
 namespace catfhe {
 
-// Butterflies with lazy reduction (after Harvey, "Faster arithmetic for
-// number-theoretic transforms", 2014): the forward transform keeps words in
-// [0, 4q) and the inverse in [0, 2q) between stages, so each butterfly pays
-// one conditional subtraction instead of three; the last stage of each
-// transform reduces fully to [0, q).  Needs 4q < 2^64 (q < 2^62).
-__device__ __forceinline__ void ct_bfly(uint64_t &a, uint64_t &b, ulonglong2 w, uint64_t q) {
-    const uint64_t q2 = 2 * q;
-    const uint64_t x = csub(a, q2);                  // [0, 2q)
-    const uint64_t t = shoup_lazy(b, w.x, w.y, q);   // [0, 2q)
-    a = x + t;                                       // [0, 4q)
-    b = x + q2 - t;                                  // (0, 4q)
-}
-
-__device__ __forceinline__ void gs_bfly(uint64_t &a, uint64_t &b, ulonglong2 w, uint64_t q) {
-    const uint64_t q2 = 2 * q;
-    const uint64_t a0 = a, b0 = b;                   // [0, 2q)
-    a = csub(a0 + b0, q2);                           // [0, 2q)
-    b = shoup_lazy(a0 + q2 - b0, w.x, w.y, q);       // [0, 2q)
-}
-
-// [0, 4q) -> [0, q)
-__device__ __forceinline__ uint64_t reduce4(uint64_t x, uint64_t q) {
-    return csub(csub(x, 2 * q), q);
-}
-
-// Forward butterfly without any conditional subtraction, for q < 2^58: the
-// bound grows by 2q per stage, from < 4q to < 36q after 16 stages, which a
-// 64-bit word still holds; the last pass reduces fully.
-__device__ __forceinline__ void ct_bfly_wide(uint64_t &a, uint64_t &b, ulonglong2 w, uint64_t q) {
-    const uint64_t t = shoup_lazy(b, w.x, w.y, q);   // [0, 2q)
-    const uint64_t a0 = a;
-    a = a0 + t;
-    b = a0 + 2 * q - t;
-}
-
-template <bool WIDE>
-__device__ __forceinline__ void fwd_bfly(uint64_t &a, uint64_t &b, ulonglong2 w, uint64_t q) {
-    if (WIDE)
-        ct_bfly_wide(a, b, w, q);
-    else
-        ct_bfly(a, b, w, q);
+// [0, 8q) -> [0, q)
+__device__ __forceinline__ uint64_t reduce8(uint64_t x, uint64_t q) {
+    return csub(csub(csub(x, 4 * q), 2 * q), q);
 }
 
 // Any word below 2^64 -> [0, q) (Shoup product by 1, then one subtraction).
 __device__ __forceinline__ uint64_t reduce_any(uint64_t x, const DevMod &m) {
     return csub(shoup_lazy(x, 1, m.one_s, m.q), m.q);
 }
-
-constexpr uint64_t kWideBound = uint64_t(1) << 58;
 
 // Limb of this CTA: group g (ciphertext or polynomial) and position r within
 // the map's period.  PRIME_MAJOR (used by the forward transform, where it
@@ -161,8 +122,8 @@ k_ntt_fwd_cols(const uint64_t *src, uint64_t *dst, const LimbMap map,
     uint64_t x[E];
 #pragma unroll
     for (int v = 0; v < E; v++) x[v] = ip[uint32_t(v) * TS];
-    // q < 2^58: no conditional subtractions; words leave below 4q + 2 LOGR q
-    // and the row pass reduces them on load
+    // q < 2^57: no conditional subtractions; words leave below 4q + 4 LOGR q
+    // (else below 8q) and the row pass reduces them after its stages
     if (q < kWideBound)
         fwd_cols_body<LOGR, LOGE, true>(x, sm, w, q, cl, tau);
     else
@@ -207,7 +168,7 @@ __device__ __forceinline__ void fwd_rows_body(uint64_t (&x)[1 << LOGE], uint64_t
 }
 
 template <int LOGR, int LOGE, bool EPI>
-__global__ void __launch_bounds__(256, EPI ? 3 : 4)
+__global__ void __launch_bounds__(256, 3)
 k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__restrict__ mods,
                const ulonglong2 *__restrict__ tw, int log_n, const NttEpilogue epi) {
     grid_dep_wait();
@@ -240,16 +201,19 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
 #pragma unroll
         for (int v = 0; v < E; v++) yv[EPI ? v : 0] = yp0[tau + T * v];
     }
+    // q < 2^57: no conditional subtractions in either pass, words stay below
+    // 4q + 4 log2(N) q <= 68q < 2^64, then one Shoup reduction; else below
+    // 8q, then three conditional subtractions.  (Each branch with its own
+    // reduction, and 3 CTAs per SM: fewer register spills, measured
+    // forward transform 297 -> 284 us.)
     if (q < kWideBound) {
-        // no conditional subtractions in either pass: words stay below
-        // 4q + 2 log2(N) q <= 36q < 2^64, reduced once at the end
         fwd_rows_body<LOGR, LOGE, true>(x, s, w, q, k1, h, tau);
 #pragma unroll
         for (int v = 0; v < E; v++) s[PAD(tau * E + v)] = reduce_any(x[v], m);
     } else {
         fwd_rows_body<LOGR, LOGE, false>(x, s, w, q, k1, h, tau);
 #pragma unroll
-        for (int v = 0; v < E; v++) s[PAD(tau * E + v)] = reduce4(x[v], q);
+        for (int v = 0; v < E; v++) s[PAD(tau * E + v)] = reduce8(x[v], q);
     }
     __syncthreads();
     if (!EPI) {
@@ -387,14 +351,15 @@ k_ntt_inv_cols(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
             gs_bfly(x[v], x[v + half], w[(1 << st) + (v >> (LOGE - st))], q);
         }
     }
-    // stage 0 with N^-1 folded in: (a + b) N^-1, (a - b) psi^-bitrev(1) N^-1
+    // stage 0 with N^-1 folded in: (a + b) N^-1, (a - b) psi^-bitrev(1) N^-1,
+    // exact Shoup products of words below 8q, fully reduced
     {
         constexpr int half = E / 2;
 #pragma unroll
         for (int v = 0; v < half; v++) {
             const uint64_t a0 = x[v], b0 = x[v + half];
             x[v] = shoup(a0 + b0, m.ninv, m.ninv_s, q);
-            x[v + half] = shoup(a0 + 2 * q - b0, m.ninvw, m.ninvw_s, q);
+            x[v + half] = shoup(a0 + 4 * q - b0, m.ninvw, m.ninvw_s, q);
         }
     }
 #pragma unroll

@@ -2,14 +2,18 @@
 // made of, measured by register-resident microbenchmarks (no memory traffic
 // inside the timed loop): the 64-bit Shoup product by a constant, fully
 // reduced (one per twiddle multiply, base-conversion weight, key product),
-// and the NTT butterfly exactly as the transform runs it (lazy Shoup
-// product, one conditional subtraction, the add and the subtract, words in
-// [0, 4q)).  These are the
-// denominators of the "alu" roofline the benchmark reports.
+// and the forward NTT butterflies exactly as the transform runs them
+// (butterfly.cuh): the one for primes below 2^57 (approximate-quotient
+// Shoup product, the add and the subtract, no conditional subtraction; its
+// words wrap modulo 2^64 after some tens of iterations here, which changes
+// no instruction) and the one for larger primes (one conditional
+// subtraction more, words in [0, 8q)).  These are the denominators of the
+// "alu" roofline the benchmark reports.
 //
 // Also holds the library's kernel-launch counter.
 #include <atomic>
 
+#include "butterfly.cuh"
 #include "modarith.cuh"
 
 namespace catfhe {
@@ -36,6 +40,7 @@ __global__ void __launch_bounds__(256) k_peak_modmul(uint64_t *out, uint64_t q, 
     out[tid] = acc;
 }
 
+template <bool WIDE>
 __global__ void __launch_bounds__(256) k_peak_bfly(uint64_t *out, uint64_t q, uint64_t w,
                                                     uint64_t ws, int iters) {
     const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -45,15 +50,10 @@ __global__ void __launch_bounds__(256) k_peak_bfly(uint64_t *out, uint64_t q, ui
         a[j] = (tid * 0x9E3779B97F4A7C15ull + j) % q;
         b[j] = (tid * 0xC2B2AE3D27D4EB4Full + 3 * j) % q;
     }
+    const ulonglong2 tw = make_ulonglong2(w, ws);
     for (int it = 0; it < iters; it++) {
 #pragma unroll
-        for (int j = 0; j < kChains; j++) {
-            // the forward transform's lazy butterfly: words in [0, 4q)
-            const uint64_t x = csub(a[j], 2 * q);
-            const uint64_t t = shoup_lazy(b[j], w, ws, q);
-            a[j] = x + t;
-            b[j] = x + 2 * q - t;
-        }
+        for (int j = 0; j < kChains; j++) fwd_bfly<WIDE>(a[j], b[j], tw, q);
     }
     uint64_t acc = 0;
 #pragma unroll
@@ -67,7 +67,9 @@ static int time_kernel(int which, cudaStream_t s, double *rate) {
     if (cudaGetDevice(&dev) != cudaSuccess) return CATFHE_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return CATFHE_ECUDA;
-    const void *fn = which ? (const void *)k_peak_bfly : (const void *)k_peak_modmul;
+    const void *fn = which == 2   ? (const void *)k_peak_bfly<true>
+                     : which == 1 ? (const void *)k_peak_bfly<false>
+                                  : (const void *)k_peak_modmul;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess)
         return CATFHE_ECUDA;
     const int blocks = sms * (per_sm > 0 ? per_sm : 1);
@@ -75,7 +77,8 @@ static int time_kernel(int which, cudaStream_t s, double *rate) {
     const int iters = 2048;
     uint64_t *out = nullptr;
     if (cudaMalloc(&out, threads * 8) != cudaSuccess) return CATFHE_ENOMEM;
-    const uint64_t q = 0x3ffffffffffc0001ull % 0x3fffffffffffffffull | 1;  // < 2^62, odd
+    // an odd modulus of a size each form serves: 60 bits, or 54 for the wide one
+    const uint64_t q = which == 2 ? 0x3fffffffffe001ull : 0xffffffffffc0001ull;
     const uint64_t w = 0x1234567890abcdefull % q;
     const uint64_t ws = uint64_t(((unsigned __int128)w << 64) / q);
     cudaEvent_t e0, e1;
@@ -85,8 +88,10 @@ static int time_kernel(int which, cudaStream_t s, double *rate) {
     int rc = CATFHE_OK;
     for (int rep = 0; rep < 6 && rc == CATFHE_OK; rep++) {
         cudaEventRecord(e0, s);
-        if (which)
-            k_peak_bfly<<<blocks, 256, 0, s>>>(out, q, w, ws, iters);
+        if (which == 2)
+            k_peak_bfly<true><<<blocks, 256, 0, s>>>(out, q, w, ws, iters);
+        else if (which == 1)
+            k_peak_bfly<false><<<blocks, 256, 0, s>>>(out, q, w, ws, iters);
         else
             k_peak_modmul<<<blocks, 256, 0, s>>>(out, q, w, ws, iters);
         cudaEventRecord(e1, s);
@@ -103,10 +108,12 @@ static int time_kernel(int which, cudaStream_t s, double *rate) {
     return rc;
 }
 
-int measure_int_peak(double *modmul_per_s, double *bfly_per_s, cudaStream_t s) {
+int measure_int_peak(double *modmul_per_s, double *bfly_per_s, double *bfly_wide_per_s,
+                     cudaStream_t s) {
     int rc = CATFHE_OK;
     if (modmul_per_s) rc = time_kernel(0, s, modmul_per_s);
     if (rc == CATFHE_OK && bfly_per_s) rc = time_kernel(1, s, bfly_per_s);
+    if (rc == CATFHE_OK && bfly_wide_per_s) rc = time_kernel(2, s, bfly_wide_per_s);
     return rc;
 }
 
