@@ -340,7 +340,8 @@ int catfhe_ntt(catfhe_ctx *ctx, uint64_t *limbs, uint32_t level, uint32_t count,
 /* Kernel watchdog.  Kernels that wait on an mbarrier for bulk copies bound
  * every wait (about one second of global time); on timeout they set a bit in
  * the context's device status word and return instead of waiting on (bit 1:
- * the inner product's copies; bit 2: catfhe_wait_selftest).  The paper has
+ * the inner product's copies; bit 2: catfhe_wait_selftest; bit 4: the
+ * ModDown / rescale combine's copy in the NTT row pass).  The paper has
  * no counterpart.  catfhe_device_status synchronises `stream`, stores the
  * word in *flags and clears it if `clear`.  catfhe_wait_selftest launches
  * one CTA whose barrier expects data that never comes: its wait gives up

@@ -84,5 +84,6 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 // Status bits of the context's status word.
 constexpr int kStatusIpWait = 1;        // inner product: a bulk-copy wait timed out
 constexpr int kStatusSelfTestWait = 2;  // catfhe_wait_selftest: its wait timed out (expected)
+constexpr int kStatusNttWait = 4;       // ModDown combine (NTT row pass): its y copy timed out
 
 }  // namespace catfhe

@@ -297,6 +297,20 @@ __device__ __forceinline__ U128 join3(const Acc3 &a0) {
 
 constexpr uint32_t kMask30 = (1u << 30) - 1;
 
+// A plan constant read from shared memory at its point of use.  The load is
+// volatile so that the compiler keeps it there: with the exact-source-count
+// instantiations fully unrolled it otherwise hoisted every constant of the
+// mixed-radix steps and spilled (332 bytes per thread at k = 8); read in
+// place, the k = 8 kernel fits in 64 registers at 4 CTAs per SM without
+// spills (batched step 1491 -> 1455 us).
+__device__ __forceinline__ uint64_t ld_plan(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.volatile.shared.u64 %0, [%1];"
+                 : "=l"(v)
+                 : "r"(uint32_t(__cvta_generic_to_shared(p))));
+    return v;
+}
+
 // Mixed-radix digits as 30-bit halves, and the centring decision (the
 // lexicographic comparison with the digits of (M-1)/2 runs from the least
 // significant digit up: the last differing digit decides).
@@ -312,10 +326,11 @@ __device__ __forceinline__ bool mixed_radix_split(const uint64_t (&r)[KMAX], uin
         al[j] = ah[j] = 0;
         if (uint32_t(j) < k) {
             Acc3 acc{0, 0, 0};
-            mac3(acc, uint32_t(r[j]) & kMask30, uint32_t(r[j] >> 30), P.C[size_t(j) * k + j]);
+            mac3(acc, uint32_t(r[j]) & kMask30, uint32_t(r[j] >> 30),
+                 ld_plan(&P.C[size_t(j) * k + j]));
 #pragma unroll
             for (int i = 0; i < KMAX; i++)
-                if (i < j) mac3(acc, al[i], ah[i], P.C[size_t(i) * k + j]);
+                if (i < j) mac3(acc, al[i], ah[i], ld_plan(&P.C[size_t(i) * k + j]));
             const uint64_t mj = P.smod[2 * j];
             const uint64_t aj = csub(redc(join3(acc), mj, P.smod[2 * j + 1]), mj);
             al[j] = uint32_t(aj) & kMask30;
@@ -384,7 +399,7 @@ __device__ __forceinline__ void load_sources(uint64_t (&a)[KMAX], uint32_t k,
 }
 
 template <int KMAX, bool MONT, bool SPLIT = false, bool EXACT = false>
-__global__ void __launch_bounds__(256, (EXACT && KMAX > 5) ? 3 : 4)
+__global__ void __launch_bounds__(256, 4)
 k_conv(const PlanList plans, const uint64_t *__restrict__ src, size_t src_item, size_t src_plan,
        uint64_t *__restrict__ dst, size_t dst_item, size_t dst_plan, uint32_t log_n) {
     grid_dep_wait();
@@ -514,8 +529,7 @@ int launch_conv(const Context &c, const PlanList &plans, const uint64_t *src, si
     if (plans.split) {
         if (plans.kmax > 8) return CATFHE_EINVAL;
         if (plans.kmin == plans.kmax) {
-            // one source count for every plan: exact instantiation (above 5
-            // sources it runs 3 CTAs per SM: under 64 registers it spills)
+            // one source count for every plan: exact instantiation
             switch (plans.kmax) {
 #define EXACTK(K)                                                                              \
     case K:                                                                                    \

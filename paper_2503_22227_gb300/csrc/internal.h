@@ -182,6 +182,7 @@ struct NttEpilogue {
     uint64_t dinv[kMapMax], dinv_s[kMapMax];
     uint32_t gathered;                          // nonzero: group g writes gout[g]
     uint64_t *gout[kGatherMax];
+    int *status;                                // the context's status word (bulk-copy wait)
 };
 int launch_ntt_fwd_combine(const Context &c, uint64_t *lift, const LimbMap &map, uint32_t n_limbs,
                            const NttEpilogue &epi, cudaStream_t s);

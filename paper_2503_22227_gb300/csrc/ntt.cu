@@ -20,6 +20,7 @@
 // every limb of the batch (blockIdx.y), so one launch covers a whole batch
 // of ciphertexts: no per-modulus kernels or streams (the paper's kernel
 // segmentation, Sec. 3.1.4, is replaced by batching).
+#include "bulk.cuh"
 #include "butterfly.cuh"
 #include "launch.cuh"
 #include "modarith.cuh"
@@ -167,7 +168,13 @@ __device__ __forceinline__ void fwd_rows_body(uint64_t (&x)[1 << LOGE], uint64_t
 #undef PAD
 }
 
-template <int LOGR, int LOGE, bool EPI>
+// EPI: 0, the plain transform; 1, the ModDown combine epilogue with its y
+// words loaded into registers before the butterflies; 2, the same epilogue
+// with the CTA's y tile (its CC chunks of R words are contiguous) brought
+// into shared memory by one bulk copy issued before the butterflies, so that
+// no registers are held for it (y 16-byte aligned and a status word, checked
+// on the host; the dynamic shared memory holds 256 E words).
+template <int LOGR, int LOGE, int EPI>
 __global__ void __launch_bounds__(256, 3)
 k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__restrict__ mods,
                const ulonglong2 *__restrict__ tw, int log_n, const NttEpilogue epi) {
@@ -175,6 +182,8 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E, CC = 256 / T;
     constexpr int RP = R + R / E;
     __shared__ uint64_t sm[CC * RP];
+    extern __shared__ __align__(16) uint64_t ytile[];
+    __shared__ __align__(8) uint64_t ybar;
     uint32_t g, r;
     limb_of<true>(map, g, r);
     const size_t N = size_t(1) << log_n;
@@ -193,13 +202,25 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
     uint64_t x[E];
 #pragma unroll
     for (int v = 0; v < E; v++) x[v] = base[tau + T * v];
-    // combine epilogue: its y words are loaded before the butterflies, so the
-    // loads overlap them (measured: 1648 -> 1613 us per batched step)
-    uint64_t yv[EPI ? E : 1];
-    if (EPI) {
+    // combine epilogue: its y words are requested before the butterflies, so
+    // the loads overlap them (measured, in registers: 1648 -> 1613 us per
+    // batched step).  The barrier is initialised and the copy issued by the
+    // same thread; the others reach the barrier after the exchange's
+    // __syncthreads.
+    uint64_t yv[EPI == 1 ? E : 1];
+    if (EPI == 1) {
         const uint64_t *yp0 = epi.y + (size_t(g) * epi.y_stride + epi.y_off[r]) * N + size_t(h) * R;
 #pragma unroll
-        for (int v = 0; v < E; v++) yv[EPI ? v : 0] = yp0[tau + T * v];
+        for (int v = 0; v < E; v++) yv[EPI == 1 ? v : 0] = yp0[tau + T * v];
+    } else if (EPI == 2 && threadIdx.x == 0) {
+        constexpr uint32_t bytes = uint32_t(CC) * R * 8;
+        mbar_init(&ybar, 1);
+        mbar_init_fence();
+        mbar_expect_tx(&ybar, bytes);
+        bulk_load(ytile,
+                  epi.y + (size_t(g) * epi.y_stride + epi.y_off[r]) * N +
+                      size_t(blockIdx.x) * CC * R,
+                  bytes, &ybar);
     }
     // q < 2^57: no conditional subtractions in either pass, words stay below
     // 4q + 4 log2(N) q <= 68q < 2^64, then one Shoup reduction; else below
@@ -216,10 +237,18 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
         for (int v = 0; v < E; v++) s[PAD(tau * E + v)] = reduce8(x[v], q);
     }
     __syncthreads();
-    if (!EPI) {
+    if (EPI == 0) {
 #pragma unroll
         for (int v = 0; v < E; v++) base[tau + T * v] = s[PAD(tau + T * v)];
     } else {
+        // a bounded wait that the CTA decides together (__syncthreads_and)
+        if (EPI == 2 && !__syncthreads_and(mbar_wait(&ybar, 0))) {
+            if (threadIdx.x == 0) {
+                atomicOr(epi.status, kStatusNttWait);
+                mbar_wait(&ybar, 0);  // a bounded time for the copy to land
+            }
+            return;
+        }
         // ModDown combine: out = (y - lift) * D^-1 (+ add), lift now in NTT form
         const size_t off = size_t(h) * R;
         uint64_t *op = (epi.gathered ? epi.gout[g] : epi.out + size_t(g) * epi.out_stride * N) +
@@ -230,7 +259,8 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
 #pragma unroll
         for (int v = 0; v < E; v++) {
             const int u = tau + T * v;
-            uint64_t o = shoup(yv[EPI ? v : 0] + q - s[PAD(u)], dv, dvs, q);
+            const uint64_t yw = EPI == 2 ? ytile[chl * R + u] : yv[EPI == 1 ? v : 0];
+            uint64_t o = shoup(yw + q - s[PAD(u)], dv, dvs, q);
             if (ap) o = add_mod(o, ap[u], q);
             op[u] = o;
         }
@@ -375,12 +405,20 @@ static int run_fwd(const Context &c, const uint64_t *src, uint64_t *dst, const L
     dim3 g1(unsigned((N >> R1) / (256 / ((1 << R1) >> E1))), n_limbs);
     launch_pdl(k_ntt_fwd_cols<R1, E1>, g1, dim3(256), 0, s, src, dst, map, c.d_mods, c.d_twf, c.log_n);
     dim3 g2(unsigned((N >> R2) / (256 / ((1 << R2) >> E2))), n_limbs);
-    if (epi)
-        launch_pdl(k_ntt_fwd_rows<R2, E2, true>, g2, dim3(256), 0, s, dst, map, c.d_mods, c.d_twf,
+    if (epi && epi->status && (reinterpret_cast<uintptr_t>(epi->y) & 15) == 0) {
+        constexpr int ybytes = 256 * (1 << E2) * 8;  // the CTA's y tile
+        if (cudaFuncSetAttribute(k_ntt_fwd_rows<R2, E2, 2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, ybytes) != cudaSuccess)
+            return CATFHE_ECUDA;
+        launch_pdl(k_ntt_fwd_rows<R2, E2, 2>, g2, dim3(256), ybytes, s, dst, map, c.d_mods,
+                   c.d_twf, c.log_n, *epi);
+    } else if (epi) {
+        launch_pdl(k_ntt_fwd_rows<R2, E2, 1>, g2, dim3(256), 0, s, dst, map, c.d_mods, c.d_twf,
                    c.log_n, *epi);
-    else
-        launch_pdl(k_ntt_fwd_rows<R2, E2, false>, g2, dim3(256), 0, s, dst, map, c.d_mods, c.d_twf,
+    } else {
+        launch_pdl(k_ntt_fwd_rows<R2, E2, 0>, g2, dim3(256), 0, s, dst, map, c.d_mods, c.d_twf,
                    c.log_n, NttEpilogue{});
+    }
     note_launches(2);
     return cudaGetLastError() == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
 }

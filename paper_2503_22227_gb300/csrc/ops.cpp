@@ -258,6 +258,7 @@ static int moddown(Context &c, uint64_t *y, uint64_t *lift, uint64_t *out, const
         e.y = y;
         e.add = add;
         e.out = out;
+        e.status = c.d_status;
         e.y_stride = uint32_t(2 * M);
         e.add_stride = uint32_t(2 * lo);
         e.out_stride = uint32_t(2 * lo);
@@ -865,6 +866,7 @@ int op_rescale(Context &c, const uint64_t *a, uint64_t *out, uint32_t level, uin
     m2.src_stride = m2.dst_stride = uint32_t(2 * lo);
     e.y = a;
     e.out = out;
+    e.status = c.d_status;
     e.y_stride = uint32_t(2 * lvl);
     e.out_stride = uint32_t(2 * lo);
     for (int p = 0; p < 2; p++)
