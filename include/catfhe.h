@@ -234,9 +234,9 @@ int catfhe_add_const(catfhe_ctx *ctx, const uint64_t *a, int64_t k, uint64_t *ou
 
 /* A plaintext polynomial for catfhe_mul_plain (Table 1 "multiply_plain"):
  * host int64[N] signed coefficients (CKKS: the encoded, scaled message;
- * BGV: a polynomial mod t) reduced mod q_0 .. q_{level-1} into the device
- * buffer pt u64[level][N], in NTT form.  ESCHEME for BFV.  Synchronises on
- * the host copy. */
+ * BFV / BGV: a polynomial mod t) reduced mod q_0 .. q_{level-1} into the
+ * device buffer pt u64[level][N], in NTT form.  Synchronises on the host
+ * copy. */
 int catfhe_plain_import(catfhe_ctx *ctx, const int64_t *coeffs, uint32_t level, uint64_t *pt,
                         void *stream);
 
@@ -263,8 +263,9 @@ int catfhe_decode_ckks(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t 
 /* Multiplication by a plaintext (Table 1 "multiply_plain"): both
  * polynomials times pt, limb by limb in NTT form; pt u64[>= level][N] from
  * catfhe_plain_import (its first `level` limbs are used).  No relinearisation;
- * a CKKS product carries the scale of a times the plaintext's scale.
- * ESCHEME for BFV. */
+ * a CKKS product carries the scale of a times the plaintext's scale.  BFV
+ * ciphertexts (coefficient form) are transformed, multiplied and transformed
+ * back inside out; out may alias a. */
 int catfhe_mul_plain(catfhe_ctx *ctx, const uint64_t *a, const uint64_t *pt, uint64_t *out,
                      uint32_t level, uint32_t count, void *stream);
 

@@ -115,8 +115,7 @@ int check_op(const catfhe_op &o) {
             return (o.level_out >= 1 && o.level_out <= o.level && o.a != o.out) ? CATFHE_OK
                                                                             : CATFHE_ELEVEL;
         case CATFHE_OP_MUL_PLAIN:
-            if (!o.b) return CATFHE_EINVAL;
-            return c.scheme == CATFHE_BFV ? CATFHE_ESCHEME : CATFHE_OK;
+            return o.b ? CATFHE_OK : CATFHE_EINVAL;
         default:
             return CATFHE_EINVAL;
     }
@@ -127,6 +126,8 @@ int check_op(const catfhe_op &o) {
 double op_cost(const catfhe_op &o) {
     const Context &c = o.ctx->c;
     const double n = double(c.n), lg = double(c.log_n), l = double(o.level), K = double(c.K);
+    if (o.op == CATFHE_OP_MUL_PLAIN && c.scheme == CATFHE_BFV)  // two transforms of 2l limbs
+        return o.count * (2 * 2 * l * n / 2 * lg + 2 * l * n);
     if (!needs_ws(o.op)) return o.count * 2 * l * n;
     if (o.op == CATFHE_OP_RESCALE) return o.count * ((2 + 2 * (l - 1)) * n / 2 * lg + 4 * l * n);
     const double M = l + K;

@@ -964,7 +964,6 @@ int op_add_const(Context &c, const uint64_t *a, int64_t k, uint64_t *out, uint32
 // (each thread reads its own coefficient before writing it), then NTT.
 int op_plain_import(Context &c, const int64_t *coeffs, uint32_t level, uint64_t *pt,
                     cudaStream_t s) {
-    if (c.scheme == CATFHE_BFV) return CATFHE_ESCHEME;
     if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
     const size_t n = c.n;
     int64_t *stage = reinterpret_cast<int64_t *>(pt + size_t(level - 1) * n);
@@ -985,12 +984,18 @@ int op_plain_import(Context &c, const int64_t *coeffs, uint32_t level, uint64_t 
     return cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
 }
 
+// CKKS / BGV rest in NTT form: one limb-wise product.  BFV rests in
+// coefficient form: the negacyclic product is NTT, limb-wise product, INTT,
+// all in out (each transform is safe in place).
 int op_mul_plain(Context &c, const uint64_t *a, const uint64_t *pt, uint64_t *out, uint32_t level,
                  uint32_t count, cudaStream_t s) {
-    if (c.scheme == CATFHE_BFV) return CATFHE_ESCHEME;
     if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
     if (count == 0) return CATFHE_OK;
-    return launch_mul_plain(c, a, pt, out, level, 2 * level * count, s);
+    if (c.scheme != CATFHE_BFV) return launch_mul_plain(c, a, pt, out, level, 2 * level * count, s);
+    const LimbMap m = map_identity(level);
+    TRY(launch_ntt_fwd(c, a, out, m, 2 * level * count, s));
+    TRY(launch_mul_plain(c, out, pt, out, level, 2 * level * count, s));
+    return launch_ntt_inv(c, out, out, m, 2 * level * count, s);
 }
 
 // Keeps the first new_level limbs of each polynomial (dropping primes keeps

@@ -469,7 +469,8 @@ def test_hoisted_rotation_errors(ckks12):
     assert e.value.code == -6
 
 
-@pytest.mark.parametrize("preset", [W.PRESETS["ckks_n12"], SMALL_BGV], ids=lambda p: p.name)
+@pytest.mark.parametrize("preset", [W.PRESETS["ckks_n12"], SMALL_BGV, SMALL_BFV],
+                         ids=lambda p: p.name)
 def test_mul_plain_matches_oracle(preset):
     pr = Pair(preset)
     rng = np.random.default_rng(41)
@@ -484,10 +485,9 @@ def test_mul_plain_matches_oracle(preset):
         out = pr.g.empty_ct(2, level)
         api.run_batch([api.make_op(api.OP_MUL_PLAIN, pr.g, da, out, b=dpt)], lanes=1)
         assert np.array_equal(pr.g.export_ct(out), got)
-    bfv = Pair(SMALL_BFV)
-    with pytest.raises(api.CatfheError) as e:
-        bfv.g.plain_import(pt, SMALL_BFV.L)
-    assert e.value.code == -6
+        # out aliasing a
+        pr.g.mul_plain(da, dpt, da)
+        assert np.array_equal(pr.g.export_ct(da), got)
 
 
 def test_zero_count_is_a_noop(ckks12):

@@ -276,18 +276,19 @@ def test_elementwise_ops_by_decryption(bgv_small, ckks_n12):
     assert np.array_equal(ctx.decrypt(keys, ctx.drop(ca, 1)), da)
 
 
-def test_mul_plain_by_decryption(bgv_small, ckks_n12):
+def test_mul_plain_by_decryption(bgv_small, bfv_small, ckks_n12):
     """Multiplication by a plaintext polynomial: decryption is linear, so
-    Dec(c pt) = Dec(c) pt in Z[X]/(X^N + 1) (mod t for BGV; exactly, as
-    integers, for small CKKS messages)."""
-    ctx, keys = bgv_small
-    n, t = ctx.n, ctx.t
-    rng = np.random.default_rng(31)
-    m = W.int_messages(rng, n, t)
-    pt = rng.integers(-3, 4, n)
-    c = ctx.encrypt(keys, m, W.seed_for("mp-bgv"))
-    want = negamul_int([int(x) for x in m], [int(x) for x in pt], t)
-    assert [int(x) for x in ctx.decrypt(keys, ctx.mul_plain(c, pt))] == want
+    Dec(c pt) = Dec(c) pt in Z[X]/(X^N + 1) (mod t for BGV and BFV, where
+    c0 + c1 s = Delta m + e becomes Delta m pt + e pt; exactly, as integers,
+    for small CKKS messages)."""
+    for (ctx, keys), tag in ((bgv_small, "bgv"), (bfv_small, "bfv")):
+        n, t = ctx.n, ctx.t
+        rng = np.random.default_rng(31)
+        m = W.int_messages(rng, n, t)
+        pt = rng.integers(-3, 4, n)
+        c = ctx.encrypt(keys, m, W.seed_for(f"mp-{tag}"))
+        want = negamul_int([int(x) for x in m], [int(x) for x in pt], t)
+        assert [int(x) for x in ctx.decrypt(keys, ctx.mul_plain(c, pt))] == want, tag
 
     ctx, keys = ckks_n12
     n = ctx.n
