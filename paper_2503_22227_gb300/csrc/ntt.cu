@@ -113,7 +113,7 @@ k_ntt_fwd_cols(const uint64_t *src, uint64_t *dst, const LimbMap map,
     uint64_t *out = dst + (size_t(g) * map.dst_stride + map.dst_off[r]) * N;
     const int p = map.prime[r];
     const uint64_t q = mods[p].q;
-    const ulonglong2 *w = tw + size_t(p) * N;
+    const ulonglong2 *wg = tw + size_t(p) * N;
     const int cl = threadIdx.x % CW, tau = threadIdx.x / CW;
     const size_t c = size_t(blockIdx.x) * CW + cl;
     const uint32_t TS = uint32_t(T * S), SS = uint32_t(S);
@@ -123,6 +123,13 @@ k_ntt_fwd_cols(const uint64_t *src, uint64_t *dst, const LimbMap map,
     uint64_t x[E];
 #pragma unroll
     for (int v = 0; v < E; v++) x[v] = ip[uint32_t(v) * TS];
+    // the column stages use twiddles 1 .. R-1 only: staged in shared memory
+    // once per CTA, after the data loads are issued (measured: forward 284 ->
+    // 278 us, inverse 298 -> 294 us for 384 limbs)
+    __shared__ ulonglong2 stw[R];
+    for (int i = threadIdx.x; i < R; i += 256) stw[i] = wg[i];
+    __syncthreads();
+    const ulonglong2 *w = stw;
     // q < 2^57: no conditional subtractions; words leave below 4q + 4 LOGR q
     // (else below 8q) and the row pass reduces them after its stages
     if (q < kWideBound)
@@ -347,7 +354,7 @@ k_ntt_inv_cols(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
     const int p = map.prime[r];
     const DevMod m = mods[p];
     const uint64_t q = m.q;
-    const ulonglong2 *w = tw + size_t(p) * N;
+    const ulonglong2 *wg = tw + size_t(p) * N;
     const int cl = threadIdx.x % CW, tau = threadIdx.x / CW;
     const size_t c = size_t(blockIdx.x) * CW + cl;
     const uint32_t TS = uint32_t(T * S), SS = uint32_t(S);
@@ -357,6 +364,13 @@ k_ntt_inv_cols(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
     uint64_t x[E];
 #pragma unroll
     for (int v = 0; v < E; v++) x[v] = ib[uint32_t(v) * SS];
+    // the column stages use twiddles 1 .. R-1 only: staged in shared memory
+    // once per CTA, after the data loads are issued (measured: forward 284 ->
+    // 278 us, inverse 298 -> 294 us for 384 limbs)
+    __shared__ ulonglong2 stw[R];
+    for (int i = threadIdx.x; i < R; i += 256) stw[i] = wg[i];
+    __syncthreads();
+    const ulonglong2 *w = stw;
 #pragma unroll
     for (int st = LOGR - 1; st >= LOGE; st--) {
         const int dist = 1 << (LOGR - 1 - st);
