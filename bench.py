@@ -538,6 +538,31 @@ def run_catfhe(args):
                     ev_out[k].record(s_out)
             torch.cuda.synchronize()
 
+        # the host link's own rates, through the same calls: uploads alone,
+        # downloads alone, both at once (two streams)
+        def link_s(up, down, reps=5):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                if up:
+                    with torch.cuda.stream(s_in):
+                        ctx.import_ct(ha, asyn, out=da[0])
+                        ctx.import_ct(hb, asyn, out=db[0])
+                if down:
+                    with torch.cuda.stream(s_out):
+                        ctx.export_into(do[1], ho[1], asyn)
+            torch.cuda.synchronize()
+            return (time.perf_counter() - t0) / reps
+
+        h2d_b, d2h_b = ha.numel() * 8 + hb.numel() * 8, ho[0].numel() * 8
+        link_s(True, True, 2)
+        t_up, t_down, t_both = link_s(True, False), link_s(False, True), link_s(True, True)
+        link = {"h2d_gbs": h2d_b / t_up / 1e9, "d2h_gbs": d2h_b / t_down / 1e9,
+                "both_gbs": (h2d_b + d2h_b) / t_both / 1e9,
+                "bound_per_s": BATCH / t_both,
+                "note": "one step's uploads and download alone and at once, through the same "
+                        "calls; bound_per_s = operations per second if a step took only its "
+                        "copies"}
         e2e_run(3)
         ke = max(3, K // 3)
         barrier(world)
@@ -550,7 +575,8 @@ def run_catfhe(args):
                "h2d_bytes_per_step": int(ha.numel() * 8 + hb.numel() * 8),
                "d2h_bytes_per_step": int(ho[0].numel() * 8),
                "note": "pinned host in/out through catfhe_ct_import / catfhe_ct_export "
-                       "(asynchronous form), pipelined over 2 buffer sets and 3 streams"}
+                       "(asynchronous form), pipelined over 2 buffer sets and 3 streams",
+               "link": link}
 
     side = None
     if not args.no_secondary:
