@@ -190,6 +190,33 @@ int catfhe_ct_import(catfhe_ctx *ctx, const uint64_t *host, uint32_t level, uint
 int catfhe_ct_export(catfhe_ctx *ctx, const uint64_t *ct, uint32_t level, uint32_t count,
                      int form, uint64_t *host, void *ws, size_t ws_bytes, void *stream);
 
+/* Bit-packed transfer form (an addition of this library; the paper moves
+ * whole words).  Each limb's N residues of prime q_i, in the at-rest form
+ * and order [count][2][level], as a little-endian bit stream of
+ * b_i = bitlen(q_i) bits per residue: residue k occupies bits
+ * [k b_i, (k+1) b_i) of the limb's N b_i / 64 words, limbs one after
+ * another.  catfhe_packed_words gives the words of `count` ciphertexts at
+ * `level` (0 on bad arguments).  import copies the packed words from host
+ * memory into `ws` (at least that many words, 16-byte aligned; NULL = the
+ * context's scratch) and unpacks them into ct; an unpacked value >= q_i is
+ * reduced by one subtraction of q_i.  export packs ct into `ws` and copies
+ * the words to host memory.  flags = 0 synchronises (as catfhe_ct_import /
+ * _export), CATFHE_FORM_ASYNC does not (the host buffer must stay valid and
+ * unchanged, or unread, until the stream's work completes).
+ * catfhe_pack_host / catfhe_unpack_host convert `polys` polynomials of
+ * `level` limbs of N = 2^log_n words between the two forms on the host,
+ * with bits[i] = b_i (1..64); pack keeps the low b_i bits of each word. */
+size_t catfhe_packed_words(const catfhe_ctx *ctx, uint32_t level, uint32_t count);
+int catfhe_ct_import_packed(catfhe_ctx *ctx, const uint64_t *packed, uint32_t level,
+                            uint32_t count, uint64_t *ct, void *ws, size_t ws_bytes, int flags,
+                            void *stream);
+int catfhe_ct_export_packed(catfhe_ctx *ctx, const uint64_t *ct, uint32_t level, uint32_t count,
+                            uint64_t *packed, void *ws, size_t ws_bytes, int flags, void *stream);
+int catfhe_pack_host(const uint8_t *bits, uint32_t level, uint32_t polys, uint32_t log_n,
+                     const uint64_t *limbs, uint64_t *packed);
+int catfhe_unpack_host(const uint8_t *bits, uint32_t level, uint32_t polys, uint32_t log_n,
+                       const uint64_t *packed, uint64_t *limbs);
+
 /* out = a + b (Table 1-3 "add"), count ciphertexts at `level`. */
 int catfhe_add(catfhe_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out,
                uint32_t level, uint32_t count, void *stream);

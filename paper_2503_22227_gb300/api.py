@@ -42,6 +42,8 @@ EXPORTS = [
     "catfhe_sub", "catfhe_mul_int", "catfhe_add_const", "catfhe_drop_level",
     "catfhe_rotate_hoisted", "catfhe_plain_import", "catfhe_mul_plain",
     "catfhe_encode_ckks", "catfhe_decode_ckks", "catfhe_device_status", "catfhe_wait_selftest",
+    "catfhe_packed_words", "catfhe_ct_import_packed", "catfhe_ct_export_packed",
+    "catfhe_pack_host", "catfhe_unpack_host",
 ]
 
 
@@ -102,6 +104,11 @@ def load(path: str = LIB_PATH):
             "catfhe_ct_uniform": (ctypes.c_int, [vp, u8p, u32, u32, vp, vp]),
             "catfhe_ct_import": (ctypes.c_int, [vp, vp, u32, u32, ctypes.c_int, vp, vp]),
             "catfhe_ct_export": (ctypes.c_int, [vp, vp, u32, u32, ctypes.c_int, vp, vp, sz, vp]),
+            "catfhe_packed_words": (sz, [vp, u32, u32]),
+            "catfhe_ct_import_packed": (ctypes.c_int, [vp, vp, u32, u32, vp, vp, sz, ctypes.c_int, vp]),
+            "catfhe_ct_export_packed": (ctypes.c_int, [vp, vp, u32, u32, vp, vp, sz, ctypes.c_int, vp]),
+            "catfhe_pack_host": (ctypes.c_int, [vp, u32, u32, u32, vp, vp]),
+            "catfhe_unpack_host": (ctypes.c_int, [vp, u32, u32, u32, vp, vp]),
             "catfhe_add": (ctypes.c_int, [vp, vp, vp, vp, u32, u32, vp]),
             "catfhe_mul_relin": (ctypes.c_int, [vp, vp, vp, vp, vp, u32, u32, vp, sz, vp]),
             "catfhe_mul_relin_rescale": (ctypes.c_int, [vp, vp, vp, vp, vp, u32, u32, vp, sz, vp]),
@@ -282,6 +289,57 @@ class Context:
                                        ctypes.c_void_p(host.data_ptr()), _ptr(ws), ws.numel(),
                                        _stream()), "catfhe_ct_export")
         return host
+
+    # ------------------------------------------------ bit-packed transfers
+    def bits(self, level: int) -> np.ndarray:
+        """Bit length of q_0 .. q_{level-1}: the packed form's field widths."""
+        return np.array([int(q).bit_length() for q in self.q[:level]], dtype=np.uint8)
+
+    def packed_words(self, level: int, count: int) -> int:
+        return int(load().catfhe_packed_words(self._h, level, count))
+
+    def pack(self, limbs, out=None):
+        """Host [count][2][level][N] residues (numpy uint64 or CPU int64
+        tensor) -> the packed words (a flat array of the same kind)."""
+        count, _, level, n = limbs.shape
+        words = self.packed_words(level, count)
+        if out is None:
+            out = (np.empty(words, dtype=np.uint64) if isinstance(limbs, np.ndarray)
+                   else _torch().empty(words, dtype=_torch().int64))
+        bits = self.bits(level)
+        _check(load().catfhe_pack_host(bits.ctypes.data_as(vp), level, 2 * count,
+                                       n.bit_length() - 1, _hptr(limbs), _hptr(out)),
+               "catfhe_pack_host")
+        return out
+
+    def unpack(self, packed, count: int, level: int) -> np.ndarray:
+        out = np.empty((count, 2, level, self.n), dtype=np.uint64)
+        bits = self.bits(level)
+        _check(load().catfhe_unpack_host(bits.ctypes.data_as(vp), level, 2 * count,
+                                         self.n.bit_length() - 1, _hptr(packed), _hptr(out)),
+               "catfhe_unpack_host")
+        return out
+
+    def import_packed(self, packed, level: int, count: int, out=None, ws=None, flags: int = 0):
+        """Packed host words -> device ciphertexts (at-rest form); ws: a
+        device buffer of at least packed_words * 8 bytes (None: the
+        context's scratch)."""
+        out = self.empty_ct(count, level) if out is None else out
+        nb = 0 if ws is None else ws.numel() * ws.element_size()
+        _check(load().catfhe_ct_import_packed(self._h, _hptr(packed), level, count, _ptr(out),
+                                              None if ws is None else _ptr(ws), nb, flags,
+                                              _stream()), "catfhe_ct_import_packed")
+        return out
+
+    def export_packed(self, ct, packed=None, ws=None, flags: int = 0):
+        count, _, level, _ = ct.shape
+        if packed is None:
+            packed = np.empty(self.packed_words(level, count), dtype=np.uint64)
+        nb = 0 if ws is None else ws.numel() * ws.element_size()
+        _check(load().catfhe_ct_export_packed(self._h, _ptr(ct), level, count, _hptr(packed),
+                                              None if ws is None else _ptr(ws), nb, flags,
+                                              _stream()), "catfhe_ct_export_packed")
+        return packed
 
     def export_ct(self, ct, form: int = FORM_COEFF) -> np.ndarray:
         count, _, level, n = ct.shape
@@ -468,6 +526,15 @@ class Context:
         _check(load().catfhe_ntt(self._h, _ptr(limbs), level, count, int(inverse), _stream()),
                "catfhe_ntt")
         return limbs
+
+
+def _hptr(x):
+    """Host address of a contiguous numpy array or CPU tensor."""
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"] and x.dtype.itemsize == 8
+        return x.ctypes.data_as(vp)
+    assert x.device.type == "cpu" and x.is_contiguous() and x.element_size() == 8
+    return ctypes.c_void_p(x.data_ptr())
 
 
 def measure_int_peak() -> tuple[float, float, float]:

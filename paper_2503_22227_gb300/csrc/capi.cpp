@@ -55,6 +55,11 @@ int op_import(Context &c, const uint64_t *host, uint32_t level, uint32_t count, 
               bool sync, uint64_t *ct, cudaStream_t s);
 int op_export(Context &c, const uint64_t *ct, uint32_t level, uint32_t count, int form,
               bool sync, uint64_t *host, void *ws, size_t ws_bytes_in, cudaStream_t s);
+int op_import_packed(Context &c, const uint64_t *host, uint32_t level, uint32_t count, bool sync,
+                     uint64_t *ct, void *ws, size_t ws_bytes, cudaStream_t s);
+int op_export_packed(Context &c, const uint64_t *ct, uint32_t level, uint32_t count, bool sync,
+                     uint64_t *host, void *ws, size_t ws_bytes, cudaStream_t s);
+size_t packed_words(const Context &c, uint32_t level);
 int op_decrypt(Context &c, const Keys &k, const uint64_t *ct, uint32_t level, uint64_t factor,
                int64_t *msg, void *ws, size_t ws_bytes_in, cudaStream_t s);
 int measure_int_peak(double *modmul_per_s, double *bfly_per_s, double *bfly_wide_per_s,
@@ -200,6 +205,77 @@ int catfhe_ct_export(catfhe_ctx *ctx, const uint64_t *ct, uint32_t level, uint32
     bool sync;
     if (!ctx || !host || !ct || !split_form(form, &base, &sync)) return CATFHE_EINVAL;
     return op_export(ctx->c, ct, level, count, base, sync, host, ws, ws_bytes, S(stream));
+}
+
+size_t catfhe_packed_words(const catfhe_ctx *ctx, uint32_t level, uint32_t count) {
+    if (!ctx || level < 1 || int(level) > ctx->c.L) return 0;
+    return size_t(2) * count * packed_words(ctx->c, level);
+}
+
+int catfhe_ct_import_packed(catfhe_ctx *ctx, const uint64_t *packed, uint32_t level,
+                            uint32_t count, uint64_t *ct, void *ws, size_t ws_bytes, int flags,
+                            void *stream) {
+    if (!ctx || !packed || !ct || (flags & ~CATFHE_FORM_ASYNC)) return CATFHE_EINVAL;
+    return op_import_packed(ctx->c, packed, level, count, !(flags & CATFHE_FORM_ASYNC), ct, ws,
+                            ws_bytes, S(stream));
+}
+
+int catfhe_ct_export_packed(catfhe_ctx *ctx, const uint64_t *ct, uint32_t level, uint32_t count,
+                            uint64_t *packed, void *ws, size_t ws_bytes, int flags, void *stream) {
+    if (!ctx || !packed || !ct || (flags & ~CATFHE_FORM_ASYNC)) return CATFHE_EINVAL;
+    return op_export_packed(ctx->c, ct, level, count, !(flags & CATFHE_FORM_ASYNC), packed, ws,
+                            ws_bytes, S(stream));
+}
+
+// Host side of the packed form (the client's encoder / decoder): plain loops
+// over the same bit layout as the device kernels.
+static bool pack_shape(const uint8_t *bits, uint32_t level, uint32_t log_n) {
+    if (!bits || level < 1 || level > 64 || log_n < 6 || log_n > 20) return false;
+    for (uint32_t i = 0; i < level; i++)
+        if (bits[i] < 1 || bits[i] > 64) return false;
+    return true;
+}
+
+int catfhe_pack_host(const uint8_t *bits, uint32_t level, uint32_t polys, uint32_t log_n,
+                     const uint64_t *limbs, uint64_t *packed) {
+    if (!pack_shape(bits, level, log_n) || (polys && (!limbs || !packed))) return CATFHE_EINVAL;
+    const uint64_t n = uint64_t(1) << log_n;
+    for (uint32_t p = 0; p < polys; p++)
+        for (uint32_t i = 0; i < level; i++) {
+            const uint32_t b = bits[i];
+            const uint64_t mask = b == 64 ? ~uint64_t(0) : (uint64_t(1) << b) - 1;
+            const uint64_t words = n * b / 64;
+            for (uint64_t w = 0; w < words; w++) packed[w] = 0;
+            for (uint64_t k = 0; k < n; k++) {
+                const uint64_t v = limbs[k] & mask, o = k * b;
+                const uint64_t w = o >> 6, sh = o & 63;
+                packed[w] |= v << sh;
+                if (sh + b > 64) packed[w + 1] |= v >> (64 - sh);
+            }
+            limbs += n;
+            packed += words;
+        }
+    return CATFHE_OK;
+}
+
+int catfhe_unpack_host(const uint8_t *bits, uint32_t level, uint32_t polys, uint32_t log_n,
+                       const uint64_t *packed, uint64_t *limbs) {
+    if (!pack_shape(bits, level, log_n) || (polys && (!limbs || !packed))) return CATFHE_EINVAL;
+    const uint64_t n = uint64_t(1) << log_n;
+    for (uint32_t p = 0; p < polys; p++)
+        for (uint32_t i = 0; i < level; i++) {
+            const uint32_t b = bits[i];
+            const uint64_t mask = b == 64 ? ~uint64_t(0) : (uint64_t(1) << b) - 1;
+            for (uint64_t k = 0; k < n; k++) {
+                const uint64_t o = k * b, w = o >> 6, sh = o & 63;
+                uint64_t v = packed[w] >> sh;
+                if (sh + b > 64) v |= packed[w + 1] << (64 - sh);
+                limbs[k] = v & mask;
+            }
+            limbs += n;
+            packed += n * b / 64;
+        }
+    return CATFHE_OK;
 }
 
 int catfhe_add(catfhe_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out,

@@ -184,6 +184,14 @@ struct NttEpilogue {
     uint64_t *gout[kGatherMax];
     int *status;                                // the context's status word (bulk-copy wait)
 };
+// Bit-packed transfer form (pack.cu): words per polynomial at `level`, and
+// the device unpack / pack of `polys` polynomials.
+size_t packed_words(const Context &c, uint32_t level);
+int launch_unpack(const Context &c, const uint64_t *packed, uint64_t *out, uint32_t level,
+                  uint32_t polys, cudaStream_t s);
+int launch_pack(const Context &c, const uint64_t *in, uint64_t *packed, uint32_t level,
+                uint32_t polys, cudaStream_t s);
+
 int launch_ntt_fwd_combine(const Context &c, uint64_t *lift, const LimbMap &map, uint32_t n_limbs,
                            const NttEpilogue &epi, cudaStream_t s);
 

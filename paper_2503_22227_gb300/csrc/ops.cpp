@@ -1346,6 +1346,37 @@ int op_export(Context &c, const uint64_t *ct, uint32_t level, uint32_t count, in
     return cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
 }
 
+// Packed transfers: the packed words are staged in the workspace (at least
+// 2 count packed_words(level) words), copied and unpacked in stream order.
+int op_import_packed(Context &c, const uint64_t *host, uint32_t level, uint32_t count, bool sync,
+                     uint64_t *ct, void *ws, size_t ws_bytes_in, cudaStream_t s) {
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    if (count == 0) return CATFHE_OK;
+    const size_t bytes = size_t(2) * count * packed_words(c, level) * 8;
+    char *base;
+    TRY(get_ws(c, ws, ws_bytes_in, bytes, &base));
+    if (cudaMemcpyAsync(base, host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return CATFHE_ECUDA;
+    TRY(launch_unpack(c, reinterpret_cast<const uint64_t *>(base), ct, level, 2 * count, s));
+    if (!sync) return CATFHE_OK;
+    return cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
+}
+
+int op_export_packed(Context &c, const uint64_t *ct, uint32_t level, uint32_t count, bool sync,
+                     uint64_t *host, void *ws, size_t ws_bytes_in, cudaStream_t s) {
+    if (level < 1 || int(level) > c.L) return CATFHE_ELEVEL;
+    if (count == 0) return CATFHE_OK;
+    const size_t bytes = size_t(2) * count * packed_words(c, level) * 8;
+    char *base;
+    TRY(get_ws(c, ws, ws_bytes_in, bytes, &base));
+    uint64_t *stage = reinterpret_cast<uint64_t *>(base);
+    TRY(launch_pack(c, ct, stage, level, 2 * count, s));
+    if (cudaMemcpyAsync(host, stage, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return CATFHE_ECUDA;
+    if (!sync) return CATFHE_OK;
+    return cudaStreamSynchronize(s) == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
+}
+
 // [c0 + c1 s]_{Q_l} per coefficient (CKKS: centred, two's complement; BFV:
 // round(t x / Q) mod t; BGV: x mod t) into res (device int64[N]), using
 // 2 level N words of scratch at base.
