@@ -27,7 +27,8 @@
  *   writes outputs during the stream-ordered work it enqueues.  `out` may
  *   alias an input of the same shape.
  * Workspace: operations that need scratch take (ws, ws_bytes): a device
- *   buffer of at least catfhe_workspace_bytes(...) bytes, 256-byte aligned,
+ *   buffer of at least catfhe_workspace_bytes(...) bytes, 256-byte aligned
+ *   (a pointer that is not even 16-byte aligned is refused with EINVAL),
  *   caller-owned, not touched after the enqueued work completes.  ws = NULL
  *   makes the library use a scratch buffer owned by the context (grown
  *   with cudaMalloc on demand; calls that share it must be ordered on one

@@ -331,7 +331,7 @@ int catfhe_run_batch(const catfhe_op *ops, uint32_t n, uint32_t lanes, void *ws,
     Plan p;
     int rc = plan_batch(ops, n, lanes, p);
     if (rc) return rc;
-    if (!ws) return CATFHE_EINVAL;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 15)) return CATFHE_EINVAL;
     if (ws_bytes < p.total) return CATFHE_EWORKSPACE;
     return run_plan(ops, p, static_cast<char *>(ws), static_cast<cudaStream_t>(stream));
 }
@@ -342,7 +342,7 @@ int catfhe_batch_capture(const catfhe_op *ops, uint32_t n, uint32_t lanes, void 
     Plan p;
     int rc = plan_batch(ops, n, lanes, p);
     if (rc) return rc;
-    if (!ws) return CATFHE_EINVAL;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 15)) return CATFHE_EINVAL;
     if (ws_bytes < p.total) return CATFHE_EWORKSPACE;
     // one uncaptured run first: builds every constant table the ops need, so
     // the captured run allocates nothing

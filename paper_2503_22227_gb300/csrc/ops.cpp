@@ -39,6 +39,9 @@ struct Bump {
 
 static int get_ws(Context &c, void *ws, size_t ws_bytes, size_t need, char **out) {
     if (ws) {
+        // kernels access the workspace in 8- and 16-byte words (and bulk
+        // copies need 16-byte alignment): refuse a pointer that is not
+        if (reinterpret_cast<uintptr_t>(ws) & 15) return CATFHE_EINVAL;
         if (ws_bytes < need) return CATFHE_EWORKSPACE;
         *out = static_cast<char *>(ws);
         return CATFHE_OK;

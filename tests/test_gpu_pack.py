@@ -65,3 +65,31 @@ def test_zero_count_is_a_noop():
     ctx.import_packed(packed, 4, 0, out=out)
     torch.cuda.synchronize()
     assert bool((out == 7).all())
+
+
+def test_misaligned_workspace_is_refused_before_any_launch():
+    """A workspace pointer that is not 16-byte aligned is refused on the host
+    (EINVAL) by the packed transfers, the key-switching calls and batches;
+    nothing is enqueued and the output is untouched."""
+    ctx = api.Context(MIXED)
+    keys = ctx.keygen(W.seed_for("pack-ws"))
+    a = ctx.ct_uniform(W.seed_for("pack-ws"), 0, 4)
+    out = torch.full_like(a, 7)
+    raw = torch.empty(1 << 24, dtype=torch.uint8, device="cuda")
+    bad = raw[8:]
+    packed = ctx.pack(ctx.export_ct(a, api.FORM_NATIVE))
+    with pytest.raises(api.CatfheError) as e:
+        ctx.import_packed(packed, 4, 1, out=out, ws=bad)
+    assert e.value.code == -1
+    import ctypes
+    L = api.load()
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = L.catfhe_mul_relin(ctx._h, keys._h, ctypes.c_void_p(a.data_ptr()),
+                            ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(out.data_ptr()), 4, 1,
+                            ctypes.c_void_p(bad.data_ptr()), bad.numel(), s)
+    assert rc == -1
+    with pytest.raises(api.CatfheError) as e:
+        api.run_batch([api.make_op(api.OP_ADD, ctx, a, out, b=a)], lanes=1, ws=bad)
+    assert e.value.code == -1
+    torch.cuda.synchronize()
+    assert bool((out == 7).all())
