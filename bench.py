@@ -222,7 +222,10 @@ def uneven_mix(api, W, R, mm_peak, n_ops=256, lanes=8, reps=5):
         gs = [c.galois_elt(r) for r in range(1, 17)]
         for g in gs:
             k.gen_galois(g)
-        tuned[log_n] = c.tune_ntt(2 * c.L * 4)
+        # one schedule per launch size class: one ciphertext (2L limbs),
+        # four, sixteen
+        tuned[log_n] = {cls: c.tune_ntt(2 * c.L * m)
+                        for cls, m in (("<=64", 1), ("<=256", 4), (">256", 16))}
         ctxs[log_n] = (c, k, gs)
     ops, keep, work = [], [], 0.0
     kinds = [api.OP_MUL_RELIN, api.OP_ROTATE, api.OP_RESCALE]
@@ -256,7 +259,8 @@ def uneven_mix(api, W, R, mm_peak, n_ops=256, lanes=8, reps=5):
             "graph_nodes": nodes, "ms_per_graph": t * 1e3,
             "one_lane_ops_per_s": n_ops / res[1][0],
             "modmul_frac_of_peak": work / t / mm_peak,
-            "ntt_schedules": {f"2^{k}": {"chosen": v[0], "us_per_schedule": v[1]}
+            "ntt_schedules": {f"2^{k}": {cls: {"chosen": cv[0], "us_per_schedule": cv[1]}
+                                         for cls, cv in v.items()}
                               for k, v in tuned.items()},
             "note": "HMult+relin / HRotate / rescale mix over N=2^13..2^16, levels 2..24; "
                     "frac = sum of per-op modular products / (time x modmul peak)"}

@@ -438,16 +438,20 @@ void catfhe_graph_destroy(catfhe_graph *graph);
 
 /* ---- NTT schedules (paper Sec. 3.1.3) ----
  * Each ring degree has a few two-pass schedules (how many of the log N
- * stages the column pass takes, and how many words each thread holds).
- * catfhe_tune_ntt times every schedule of ctx's ring degree on `limbs`
- * limbs (forward + inverse, best of five, synchronises `stream`), keeps the
- * fastest for all later work of ctx and writes its index to *chosen and each
- * schedule's time in microseconds to us[] (either may be NULL).
- * catfhe_ntt_schedule reports the schedule in use, how many exist and its
- * shape {column log size, column log words/thread, row log size, row log
- * words/thread}; catfhe_set_ntt_schedule picks one by index. */
+ * stages the column pass takes, and how many words each thread holds).  The
+ * context keeps one choice per launch size class: launches of up to 64
+ * limbs, up to 256, and more.  catfhe_tune_ntt times every schedule of
+ * ctx's ring degree on `limbs` limbs (rounded up to whole groups of L;
+ * forward + inverse, best of five, synchronises `stream`), keeps the
+ * fastest for later launches of that size class and writes its index to
+ * *chosen and each schedule's time in microseconds to us[] (either may be
+ * NULL).  catfhe_ntt_schedule reports the schedule used for launches of
+ * `limbs` limbs, how many exist and its shape {column log size, column log
+ * words/thread, row log size, row log words/thread};
+ * catfhe_set_ntt_schedule picks one by index for every class. */
 int catfhe_tune_ntt(catfhe_ctx *ctx, uint32_t limbs, void *stream, int32_t *chosen, float *us);
-int catfhe_ntt_schedule(const catfhe_ctx *ctx, int32_t *index, int32_t *count, int32_t shape[4]);
+int catfhe_ntt_schedule(const catfhe_ctx *ctx, uint32_t limbs, int32_t *index, int32_t *count,
+                        int32_t shape[4]);
 int catfhe_set_ntt_schedule(catfhe_ctx *ctx, int32_t index);
 
 /* Workspace bytes that `op` needs for `count` ciphertexts at `level`. */

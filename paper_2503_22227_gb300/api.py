@@ -134,7 +134,7 @@ def load(path: str = LIB_PATH):
             "catfhe_graph_nodes": (sz, [vp]),
             "catfhe_graph_destroy": (None, [vp]),
             "catfhe_tune_ntt": (ctypes.c_int, [vp, u32, vp, ctypes.POINTER(ctypes.c_int32), vp]),
-            "catfhe_ntt_schedule": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32),
+            "catfhe_ntt_schedule": (ctypes.c_int, [vp, u32, ctypes.POINTER(ctypes.c_int32),
                                                    ctypes.POINTER(ctypes.c_int32), vp]),
             "catfhe_set_ntt_schedule": (ctypes.c_int, [vp, ctypes.c_int32]),
             "catfhe_sub": (ctypes.c_int, [vp, vp, vp, vp, u32, u32, vp]),
@@ -502,19 +502,22 @@ class Context:
         return out
 
     def tune_ntt(self, limbs: int):
-        """Times every NTT schedule of this ring degree; keeps the fastest."""
+        """Times every NTT schedule of this ring degree on `limbs` limbs; keeps
+        the fastest for launches of that size class."""
         chosen = ctypes.c_int32()
         us = (ctypes.c_float * 8)()
         _check(load().catfhe_tune_ntt(self._h, limbs, _stream(), ctypes.byref(chosen), us),
                "catfhe_tune_ntt")
-        idx, count, shape = self.ntt_schedule()
+        idx, count, shape = self.ntt_schedule(limbs)
         return chosen.value, [round(us[i], 2) for i in range(count)]
 
-    def ntt_schedule(self):
+    def ntt_schedule(self, limbs: int = 1 << 20):
+        """(index, count, shape) of the schedule used for launches of `limbs`
+        limbs (default: the largest size class)."""
         idx, count = ctypes.c_int32(), ctypes.c_int32()
         shape = (ctypes.c_int32 * 4)()
-        _check(load().catfhe_ntt_schedule(self._h, ctypes.byref(idx), ctypes.byref(count), shape),
-               "catfhe_ntt_schedule")
+        _check(load().catfhe_ntt_schedule(self._h, limbs, ctypes.byref(idx), ctypes.byref(count),
+                                          shape), "catfhe_ntt_schedule")
         return idx.value, count.value, list(shape)
 
     def set_ntt_schedule(self, index: int):

@@ -399,13 +399,15 @@ int catfhe_tune_ntt(catfhe_ctx *ctx, uint32_t limbs, void *stream, int32_t *chos
     return rc;
 }
 
-int catfhe_ntt_schedule(const catfhe_ctx *ctx, int32_t *index, int32_t *count, int32_t shape[4]) {
-    if (!ctx) return CATFHE_EINVAL;
-    if (index) *index = ctx->c.ntt_sched;
+int catfhe_ntt_schedule(const catfhe_ctx *ctx, uint32_t limbs, int32_t *index, int32_t *count,
+                        int32_t shape[4]) {
+    if (!ctx || limbs == 0) return CATFHE_EINVAL;
+    const int sched = ctx->c.ntt_sched[ntt_class(limbs)];
+    if (index) *index = sched;
     if (count) *count = ntt_schedule_count(ctx->c.log_n);
     if (shape) {
         int s[4];
-        ntt_schedule_shape(ctx->c.log_n, ctx->c.ntt_sched, s);
+        ntt_schedule_shape(ctx->c.log_n, sched, s);
         for (int i = 0; i < 4; i++) shape[i] = s[i];
     }
     return CATFHE_OK;
@@ -413,7 +415,7 @@ int catfhe_ntt_schedule(const catfhe_ctx *ctx, int32_t *index, int32_t *count, i
 
 int catfhe_set_ntt_schedule(catfhe_ctx *ctx, int32_t index) {
     if (!ctx || index < 0 || index >= ntt_schedule_count(ctx->c.log_n)) return CATFHE_EINVAL;
-    ctx->c.ntt_sched = index;
+    for (int k = 0; k < kNttClasses; k++) ctx->c.ntt_sched[k] = index;
     return CATFHE_OK;
 }
 

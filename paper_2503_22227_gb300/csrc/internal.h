@@ -140,7 +140,9 @@ struct Context {
     std::map<std::string, uint32_t> plan_sizes;  // words
     Scratch scratch;
     int device = 0;
-    int ntt_sched = 0;  // NTT schedule index for this ring degree (see ntt.cu)
+    // NTT schedule index for this ring degree (see ntt.cu), per launch size
+    // class (ntt_class)
+    int ntt_sched[3] = {0, 0, 0};
     int *d_status = nullptr;    // device status word: bits of kernels' timed-out waits
     double2 *d_enc = nullptr;   // CKKS encoder tables (encode.cu), built on first use
     uint32_t *d_slot = nullptr;
@@ -195,6 +197,10 @@ int launch_pack(const Context &c, const uint64_t *in, uint64_t *packed, uint32_t
 int launch_ntt_fwd_combine(const Context &c, uint64_t *lift, const LimbMap &map, uint32_t n_limbs,
                            const NttEpilogue &epi, cudaStream_t s);
 
+// Launch size classes of the NTT schedule choice: up to 64 limbs in one
+// launch (about one ciphertext), up to 256, more.
+constexpr int kNttClasses = 3;
+inline int ntt_class(uint32_t limbs) { return limbs <= 64 ? 0 : limbs <= 256 ? 1 : 2; }
 int ntt_schedule_count(int log_n);
 void ntt_schedule_shape(int log_n, int sched, int shape[4]);
 int tune_ntt(Context &c, uint32_t limbs, cudaStream_t s, int *chosen, float *us_out);

@@ -479,8 +479,9 @@ void ntt_schedule_shape(int log_n, int sched, int shape[4]) {
 static int fwd_dispatch(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
                         uint32_t n_limbs, cudaStream_t s, const NttEpilogue *epi) {
     if (n_limbs == 0) return CATFHE_OK;
+    const int sched = c.ntt_sched[ntt_class(n_limbs)];
 #define FWD(LN, S, A, B, C, D) \
-    if (c.log_n == LN && c.ntt_sched == S) return run_fwd<A, B, C, D>(c, src, dst, map, n_limbs, s, epi);
+    if (c.log_n == LN && sched == S) return run_fwd<A, B, C, D>(c, src, dst, map, n_limbs, s, epi);
     NTT_SCHEDULES(FWD)
 #undef FWD
     return CATFHE_EINVAL;
@@ -499,15 +500,17 @@ int launch_ntt_fwd_combine(const Context &c, uint64_t *lift, const LimbMap &map,
 int launch_ntt_inv(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
                    uint32_t n_limbs, cudaStream_t s) {
     if (n_limbs == 0) return CATFHE_OK;
+    const int sched = c.ntt_sched[ntt_class(n_limbs)];
 #define INV(LN, S, A, B, C, D) \
-    if (c.log_n == LN && c.ntt_sched == S) return run_inv<A, B, C, D>(c, src, dst, map, n_limbs, s);
+    if (c.log_n == LN && sched == S) return run_inv<A, B, C, D>(c, src, dst, map, n_limbs, s);
     NTT_SCHEDULES(INV)
 #undef INV
     return CATFHE_EINVAL;
 }
 
-// Times every schedule of this ring degree on `limbs` limbs (a forward and an
-// inverse transform each, best of five) and keeps the fastest in the context.
+// Times every schedule of this ring degree on `limbs` limbs (rounded up to
+// whole groups of L; a forward and an inverse transform each, best of five)
+// and keeps the fastest in the context for launches of that size class.
 int tune_ntt(Context &c, uint32_t limbs, cudaStream_t s, int *chosen, float *us_out) {
     const int count = ntt_schedule_count(c.log_n);
     if (count == 0 || limbs == 0) return CATFHE_EINVAL;
@@ -527,11 +530,12 @@ int tune_ntt(Context &c, uint32_t limbs, cudaStream_t s, int *chosen, float *us_
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int keep = c.ntt_sched;
+    const int cls = ntt_class(groups * L);
+    const int keep = c.ntt_sched[cls];
     int best = keep;
     float best_ms = 1e30f;
     for (int k = 0; k < count && rc == CATFHE_OK; k++) {
-        c.ntt_sched = k;
+        c.ntt_sched[cls] = k;
         float t_min = 1e30f;
         for (int rep = 0; rep < 6 && rc == CATFHE_OK; rep++) {
             cudaEventRecord(e0, s);
@@ -549,8 +553,8 @@ int tune_ntt(Context &c, uint32_t limbs, cudaStream_t s, int *chosen, float *us_
             best = k;
         }
     }
-    c.ntt_sched = rc == CATFHE_OK ? best : keep;
-    if (chosen) *chosen = c.ntt_sched;
+    c.ntt_sched[cls] = rc == CATFHE_OK ? best : keep;
+    if (chosen) *chosen = c.ntt_sched[cls];
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(buf);

@@ -34,9 +34,15 @@ def test_every_ntt_schedule_matches_oracle(log_n):
             assert np.array_equal(got[0, i], want[i]), (k, i)
         ctx.ntt(dev, inverse=True)
         assert np.array_equal(dev.cpu().numpy().view(np.uint64), host), k
+    # one choice per launch size class: tuning the small class leaves the
+    # large one as it was
+    ctx.set_ntt_schedule(count - 1)
     chosen, times = ctx.tune_ntt(3 * 8)
     assert 0 <= chosen < count and len(times) == count and all(t > 0 for t in times)
-    assert ctx.ntt_schedule()[0] == chosen
+    assert ctx.ntt_schedule(24)[0] == chosen
+    assert ctx.ntt_schedule(3 * 200)[0] == count - 1
+    big, _ = ctx.tune_ntt(3 * 100)
+    assert ctx.ntt_schedule(300)[0] == big and ctx.ntt_schedule(24)[0] == chosen
 
 
 def _ctx(preset, rots):
