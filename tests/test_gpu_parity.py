@@ -544,3 +544,38 @@ def test_split_and_alternating_paths_equal_single_calls():
     hoisted = ctx.rotate_hoisted(keys, a[:2], gs)
     for r, g in enumerate(gs):
         assert torch.equal(hoisted[r], ctx.rotate(keys, a[:2], g)), g
+
+
+# ---------------------------------------------------------------- conversion layouts at the edges
+# The key-switching presets above keep digits of at most 8 primes below 2^60,
+# so their exact conversions run in the split-weight Montgomery layout.  These
+# reach the other layouts and the largest sizes:
+#  - 12 primes per digit: Montgomery constants without split weights;
+#  - 32 primes in one digit (the most a context holds);
+#  - 61-bit primes: ModUp's constants no longer sum below 2^64, so the
+#    exact layout (128-bit sums reduced by Shoup products) runs; ModDown's
+#    three 61-bit sources stay in the Montgomery layout.
+EDGE_PRESETS = [
+    W.Preset("ckks_wide_digit", W.CKKS, 12, (50,) * 12, (60, 60), 1, log_n_max=12),
+    W.Preset("ckks_max_l", W.CKKS, 12, (40,) * 32, (50, 50), 1, log_n_max=12),
+    W.Preset("ckks_61bit", W.CKKS, 12, (61,) * 10, (61, 61), 1, log_n_max=12),
+]
+
+
+@pytest.mark.parametrize("preset", EDGE_PRESETS, ids=lambda p: p.name)
+def test_conversion_layouts_at_the_edges_match_oracle(preset):
+    pr = Pair(preset, galois=(5,))
+    L = preset.L
+    for level in (L, L - 1, 2):
+        a, b = _uniform_pair(pr, level, 2, f"edge-{preset.name}-{level}")
+        da, db = pr.g.import_ct(a), pr.g.import_ct(b)
+        got = pr.g.export_ct(pr.g.mul_relin(pr.gk, da, db))
+        want = [pr.o.mul_relin(pr.ok, a[c], b[c]) for c in range(2)]
+        for c in range(2):
+            assert np.array_equal(got[c], want[c]), (level, c)
+        got = pr.g.export_ct(pr.g.mul_relin_rescale(pr.gk, da, db))
+        for c in range(2):
+            assert np.array_equal(got[c], pr.o.rescale(want[c])), (level, c)
+        got = pr.g.export_ct(pr.g.rotate(pr.gk, da, 5))
+        for c in range(2):
+            assert np.array_equal(got[c], pr.o.rotate(pr.ok, a[c], 5)), (level, c)
