@@ -119,9 +119,10 @@ class Clocks:
 
 # ---------------------------------------------------------------- CPU oracle leg
 
-def oracle_op_seconds(n_ops: int = 1):
+def oracle_op_seconds(n_ops: int = 1, warm: int = 0):
     """Times the CPU oracle on `n_ops` HMult+relin+rescale of the workload
-    (one ciphertext pair each), single-threaded, keygen untimed."""
+    (one ciphertext pair each), single-threaded, after `warm` untimed ones;
+    keygen untimed."""
     import oracle
     from paper_2503_22227_gb300 import workloads as W
     p = W.PRESETS[PRESET]
@@ -129,34 +130,38 @@ def oracle_op_seconds(n_ops: int = 1):
     keys = ctx.keygen(W.seed_for("bench-keys"))
     seed = W.seed_for("bench-inputs")
     times = []
-    for i in range(n_ops):
+    for i in range(warm + n_ops):
         a = ctx.ct_uniform(seed, 2 * i, p.L)
         b = ctx.ct_uniform(seed, 2 * i + 1, p.L)
         t0 = time.perf_counter()
         ctx.rescale(ctx.mul_relin(keys, a, b))
-        times.append(time.perf_counter() - t0)
+        if i >= warm:
+            times.append(time.perf_counter() - t0)
     return times
 
 
 def _ref_worker(args):
-    idx, n_ops = args
-    return oracle_op_seconds(n_ops)
+    idx, n_ops, warm = args
+    return oracle_op_seconds(n_ops, warm)
 
 
-def oracle_pool(k: int):
+def oracle_pool(k: int, warm: int = 0):
     """k oracle operations spread over min(k, cores) spawned processes (a
-    spawned pool: safe after CUDA has been initialised in this process).
-    Returns (ops/s from the slowest worker's op time, processes, wall s)."""
+    spawned pool: safe after CUDA has been initialised in this process),
+    each process first running ceil(warm / processes) untimed ones.
+    Returns (ops/s from the slowest worker's op time, processes, wall s,
+    s per op, warm-up ops run)."""
     import multiprocessing as mp
     cores = os.cpu_count() or 1
     procs = max(1, min(k, cores))
     per = [k // procs + (1 if i < k % procs else 0) for i in range(procs)]
+    w = -(-warm // procs) if warm > 0 else 0
     t0 = time.perf_counter()
     with mp.get_context("spawn").Pool(procs) as pool:
-        results = pool.map(_ref_worker, [(i, per[i]) for i in range(procs)])
+        results = pool.map(_ref_worker, [(i, per[i], w) for i in range(procs)])
     wall = time.perf_counter() - t0
     busy = max(sum(r) for r in results)
-    return k / busy, procs, wall, busy / max(per)
+    return k / busy, procs, wall, busy / max(per), w * procs
 
 
 def run_reference(args):
@@ -168,10 +173,10 @@ def run_reference(args):
     cores = os.cpu_count() or 1
     # one operation per step, at most two per core, so the run stays bounded
     k = max(1, min(args.steps, 2 * cores))
-    value, procs, wall, per_op = oracle_pool(k)
+    value, procs, wall, per_op, warmed = oracle_pool(k, args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-        "n_gpus": args.gpus, "steps": k, "warmup": 0, "ms_per_step": 1e3 * per_op,
+        "n_gpus": args.gpus, "steps": k, "warmup": warmed, "ms_per_step": 1e3 * per_op,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
         "config": {"workload": "ckks_n16: CKKS N=2^16 L=24 K=4 dnum=3, HMult+relin+rescale "
@@ -179,7 +184,8 @@ def run_reference(args):
                    "dnum": 3},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
                          "sample": f"{k} HMult+relin+rescale ops (one pair each; steps capped at "
-                                   f"2 per core) over {procs} processes; keygen untimed; "
+                                   f"2 per core) over {procs} processes, after {warmed} untimed "
+                                   f"warm-up ops (one or more per process); keygen untimed; "
                                    f"wall {wall:.1f}s"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -611,7 +617,7 @@ def run_catfhe(args):
     if world == 1 and not args.no_cpu_baseline:
         # the oracle as it stands on every host core (one op per process),
         # and on one thread
-        pv, procs, wall, _ = oracle_pool(os.cpu_count() or 1)
+        pv, procs, wall, _, _ = oracle_pool(os.cpu_count() or 1)
         ts = oracle_op_seconds(1)
         cpu = {"value": pv, "unit": UNIT, "cores": procs, "kind": "oracle",
                "sample": f"{procs} HMult+relin+rescale ops of the workload (N=2^16, L=24; one "
