@@ -44,14 +44,30 @@ k_tensor(const TensorArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
     const size_t l0 = size_t(i) * n + x, l1 = (size_t(A.limbs) + i) * n + x;
     const ulonglong2 a0 = ld2(a + l0), a1 = ld2(a + l1), b0 = ld2(b + l0), b1 = ld2(b + l1);
     const size_t o = item * A.out_item + size_t(i) * n + x;
-    st2(A.d0 + o, mul_mod(a0.x, b0.x, m), mul_mod(a0.y, b0.y, m));
+    // b in Montgomery form (b 2^64 mod q, in [0, 2q), one Shoup product each),
+    // then one Montgomery reduction per output: a b' < 2q^2 and the d1 sum
+    // < 4q^2, both below 2^64 q, so REDC returns a b in [0, 2q)
+    // (measured: batched step 1438.5 -> 1435.2 us against two Shoup products
+    // per 128-bit reduction)
+    const uint64_t q = m.q;
+    const ulonglong2 c0 = make_ulonglong2(shoup_lazy(b0.x, m.r64, m.r64_s, q),
+                                          shoup_lazy(b0.y, m.r64, m.r64_s, q));
+    const ulonglong2 c1 = make_ulonglong2(shoup_lazy(b1.x, m.r64, m.r64_s, q),
+                                          shoup_lazy(b1.y, m.r64, m.r64_s, q));
+    U128 p0{0, 0}, p1{0, 0};
+    mac(p0, a0.x, c0.x);
+    mac(p1, a0.y, c0.y);
+    st2(A.d0 + o, csub(redc(p0, q, m.qinv), q), csub(redc(p1, q, m.qinv), q));
     U128 s0{0, 0}, s1{0, 0};
-    mac(s0, a0.x, b1.x);
-    mac(s0, a1.x, b0.x);
-    mac(s1, a0.y, b1.y);
-    mac(s1, a1.y, b0.y);
-    st2(A.d1 + o, reduce128(s0, m), reduce128(s1, m));
-    st2(A.d2 + o, mul_mod(a1.x, b1.x, m), mul_mod(a1.y, b1.y, m));
+    mac(s0, a0.x, c1.x);
+    mac(s0, a1.x, c0.x);
+    mac(s1, a0.y, c1.y);
+    mac(s1, a1.y, c0.y);
+    st2(A.d1 + o, csub(redc(s0, q, m.qinv), q), csub(redc(s1, q, m.qinv), q));
+    U128 r0{0, 0}, r1{0, 0};
+    mac(r0, a1.x, c1.x);
+    mac(r1, a1.y, c1.y);
+    st2(A.d2 + o, csub(redc(r0, q, m.qinv), q), csub(redc(r1, q, m.qinv), q));
 }
 
 int launch_tensor(const Context &c, const TensorArgs &a, uint32_t count, cudaStream_t s) {
