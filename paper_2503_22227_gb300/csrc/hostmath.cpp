@@ -23,12 +23,9 @@ uint64_t h_powmod(uint64_t a, uint64_t e, uint64_t m) {
 
 // Inverse modulo m by the extended Euclidean algorithm (0 if none).
 uint64_t h_invmod(uint64_t a, uint64_t m) {
-    int64_t s0 = 1, s1 = 0;
     uint64_t r0 = a % m, r1 = m;
-    // track coefficients with signed 128-bit to avoid overflow
+    // the Bezout coefficient of a, tracked in signed 128 bits (no overflow)
     __int128 x0 = 1, x1 = 0;
-    (void)s0;
-    (void)s1;
     while (r1) {
         uint64_t qt = r0 / r1;
         uint64_t r2 = r0 - qt * r1;

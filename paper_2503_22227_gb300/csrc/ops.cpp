@@ -354,7 +354,6 @@ static size_t ks_ws(const Context &c, uint32_t count, int level, bool fused) {
 
 size_t ws_bytes(const Context &c, int op, uint32_t level, uint32_t count) {
     Bump b{nullptr};
-    KsBufs k{};
     const size_t n = c.n;
     switch (op) {
         case CATFHE_OP_MUL_RELIN:
