@@ -23,8 +23,10 @@
  *   [0, q_i).  At rest, CKKS and BGV ciphertexts are in NTT (evaluation)
  *   form and BFV ciphertexts in coefficient form; the NTT order is
  *   internal.  catfhe_ct_export gives the coefficient form.
- *   Device buffers are caller-owned; the library only reads inputs and
- *   writes outputs during the stream-ordered work it enqueues.  `out` may
+ *   Device buffers are caller-owned and 16-byte aligned (a pointer that is
+ *   not is refused with EINVAL before any work is enqueued); the library only
+ *   reads inputs and writes outputs during the stream-ordered work it
+ *   enqueues.  `out` may
  *   alias an input of the same shape.
  * Workspace: operations that need scratch take (ws, ws_bytes): a device
  *   buffer of at least catfhe_workspace_bytes(...) bytes, 256-byte aligned

@@ -82,8 +82,12 @@ bool needs_ws(int op) {
            op == CATFHE_OP_ROTATE || op == CATFHE_OP_RESCALE;
 }
 
+// A device buffer not 16-byte aligned is refused (kernels use 16-byte words).
+static bool misaligned(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) != 0; }
+
 int check_op(const catfhe_op &o) {
     if (!o.ctx || !o.a || !o.out) return CATFHE_EINVAL;
+    if (misaligned(o.a) || misaligned(o.out) || (o.b && misaligned(o.b))) return CATFHE_EINVAL;
     const Context &c = o.ctx->c;
     if (o.level < 1 || int(o.level) > c.L) return CATFHE_ELEVEL;
     switch (o.op) {

@@ -76,6 +76,11 @@ static bool keys_ok(const catfhe_ctx *ctx, const catfhe_keys *k) {
     return ctx && k && k->k && k->owner == ctx;
 }
 
+// Device buffers of the caller: kernels read and write them in 8- and 16-byte
+// words, so a pointer that is not 16-byte aligned is refused (EINVAL) before
+// anything is enqueued, as is a null one.
+static bool dev(const void *p) { return p && !(reinterpret_cast<uintptr_t>(p) & 15); }
+
 extern "C" {
 
 const char *catfhe_strerror(int code) {
@@ -174,13 +179,13 @@ int catfhe_keys_export(catfhe_ctx *ctx, const catfhe_keys *keys, uint64_t key_id
 
 int catfhe_encrypt(catfhe_ctx *ctx, const catfhe_keys *keys, const int64_t *msg,
                    const uint8_t seed[32], uint64_t *ct, void *stream) {
-    if (!keys_ok(ctx, keys) || !msg || !seed || !ct) return CATFHE_EINVAL;
+    if (!keys_ok(ctx, keys) || !msg || !seed || !dev(ct)) return CATFHE_EINVAL;
     return op_encrypt(ctx->c, *keys->k, msg, seed, ct, S(stream));
 }
 
 int catfhe_ct_uniform(catfhe_ctx *ctx, const uint8_t seed[32], uint32_t index, uint32_t level,
                       uint64_t *ct, void *stream) {
-    if (!ctx || !seed || !ct) return CATFHE_EINVAL;
+    if (!ctx || !seed || !dev(ct)) return CATFHE_EINVAL;
     return op_ct_uniform(ctx->c, seed, index, level, ct, S(stream));
 }
 
@@ -195,7 +200,7 @@ int catfhe_ct_import(catfhe_ctx *ctx, const uint64_t *host, uint32_t level, uint
                      int form, uint64_t *ct, void *stream) {
     int base;
     bool sync;
-    if (!ctx || !host || !ct || !split_form(form, &base, &sync)) return CATFHE_EINVAL;
+    if (!ctx || !host || !dev(ct) || !split_form(form, &base, &sync)) return CATFHE_EINVAL;
     return op_import(ctx->c, host, level, count, base, sync, ct, S(stream));
 }
 
@@ -203,7 +208,7 @@ int catfhe_ct_export(catfhe_ctx *ctx, const uint64_t *ct, uint32_t level, uint32
                      int form, uint64_t *host, void *ws, size_t ws_bytes, void *stream) {
     int base;
     bool sync;
-    if (!ctx || !host || !ct || !split_form(form, &base, &sync)) return CATFHE_EINVAL;
+    if (!ctx || !host || !dev(ct) || !split_form(form, &base, &sync)) return CATFHE_EINVAL;
     return op_export(ctx->c, ct, level, count, base, sync, host, ws, ws_bytes, S(stream));
 }
 
@@ -215,14 +220,14 @@ size_t catfhe_packed_words(const catfhe_ctx *ctx, uint32_t level, uint32_t count
 int catfhe_ct_import_packed(catfhe_ctx *ctx, const uint64_t *packed, uint32_t level,
                             uint32_t count, uint64_t *ct, void *ws, size_t ws_bytes, int flags,
                             void *stream) {
-    if (!ctx || !packed || !ct || (flags & ~CATFHE_FORM_ASYNC)) return CATFHE_EINVAL;
+    if (!ctx || !packed || !dev(ct) || (flags & ~CATFHE_FORM_ASYNC)) return CATFHE_EINVAL;
     return op_import_packed(ctx->c, packed, level, count, !(flags & CATFHE_FORM_ASYNC), ct, ws,
                             ws_bytes, S(stream));
 }
 
 int catfhe_ct_export_packed(catfhe_ctx *ctx, const uint64_t *ct, uint32_t level, uint32_t count,
                             uint64_t *packed, void *ws, size_t ws_bytes, int flags, void *stream) {
-    if (!ctx || !packed || !ct || (flags & ~CATFHE_FORM_ASYNC)) return CATFHE_EINVAL;
+    if (!ctx || !packed || !dev(ct) || (flags & ~CATFHE_FORM_ASYNC)) return CATFHE_EINVAL;
     return op_export_packed(ctx->c, ct, level, count, !(flags & CATFHE_FORM_ASYNC), packed, ws,
                             ws_bytes, S(stream));
 }
@@ -280,38 +285,38 @@ int catfhe_unpack_host(const uint8_t *bits, uint32_t level, uint32_t polys, uint
 
 int catfhe_add(catfhe_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out,
                uint32_t level, uint32_t count, void *stream) {
-    if (!ctx || !a || !b || !out) return CATFHE_EINVAL;
+    if (!ctx || !dev(a) || !dev(b) || !dev(out)) return CATFHE_EINVAL;
     return op_add(ctx->c, a, b, out, level, count, S(stream));
 }
 
 int catfhe_sub(catfhe_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out,
                uint32_t level, uint32_t count, void *stream) {
-    if (!ctx || !a || !b || !out) return CATFHE_EINVAL;
+    if (!ctx || !dev(a) || !dev(b) || !dev(out)) return CATFHE_EINVAL;
     return op_sub(ctx->c, a, b, out, level, count, S(stream));
 }
 
 int catfhe_mul_int(catfhe_ctx *ctx, const uint64_t *a, int64_t k, uint64_t *out, uint32_t level,
                    uint32_t count, void *stream) {
-    if (!ctx || !a || !out) return CATFHE_EINVAL;
+    if (!ctx || !dev(a) || !dev(out)) return CATFHE_EINVAL;
     return op_mul_int(ctx->c, a, k, out, level, count, S(stream));
 }
 
 int catfhe_add_const(catfhe_ctx *ctx, const uint64_t *a, int64_t k, uint64_t *out,
                      uint32_t level, uint32_t count, void *stream) {
-    if (!ctx || !a || !out) return CATFHE_EINVAL;
+    if (!ctx || !dev(a) || !dev(out)) return CATFHE_EINVAL;
     return op_add_const(ctx->c, a, k, out, level, count, S(stream));
 }
 
 int catfhe_drop_level(catfhe_ctx *ctx, const uint64_t *a, uint32_t level, uint32_t new_level,
                       uint64_t *out, uint32_t count, void *stream) {
-    if (!ctx || !a || !out || a == out) return CATFHE_EINVAL;
+    if (!ctx || !dev(a) || !dev(out) || a == out) return CATFHE_EINVAL;
     return op_drop_level(ctx->c, a, level, new_level, out, count, S(stream));
 }
 
 int catfhe_mul_relin(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
                      const uint64_t *b, uint64_t *out, uint32_t level, uint32_t count,
                      void *ws, size_t ws_bytes, void *stream) {
-    if (!keys_ok(ctx, keys) || !a || !b || !out) return CATFHE_EINVAL;
+    if (!keys_ok(ctx, keys) || !dev(a) || !dev(b) || !dev(out)) return CATFHE_EINVAL;
     return op_mul_relin(ctx->c, *keys->k, a, b, out, level, count, false, ws, ws_bytes, S(stream),
                         nullptr, true);
 }
@@ -319,7 +324,7 @@ int catfhe_mul_relin(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a
 int catfhe_mul_relin_rescale(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
                              const uint64_t *b, uint64_t *out, uint32_t level, uint32_t count,
                              void *ws, size_t ws_bytes, void *stream) {
-    if (!keys_ok(ctx, keys) || !a || !b || !out) return CATFHE_EINVAL;
+    if (!keys_ok(ctx, keys) || !dev(a) || !dev(b) || !dev(out)) return CATFHE_EINVAL;
     return op_mul_relin(ctx->c, *keys->k, a, b, out, level, count, true, ws, ws_bytes, S(stream),
                         nullptr, true);
 }
@@ -327,7 +332,7 @@ int catfhe_mul_relin_rescale(catfhe_ctx *ctx, const catfhe_keys *keys, const uin
 int catfhe_rotate(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *a,
                   uint64_t galois_elt, uint64_t *out, uint32_t level, uint32_t count, void *ws,
                   size_t ws_bytes, void *stream) {
-    if (!keys_ok(ctx, keys) || !a || !out) return CATFHE_EINVAL;
+    if (!keys_ok(ctx, keys) || !dev(a) || !dev(out)) return CATFHE_EINVAL;
     return op_rotate(ctx->c, *keys->k, a, galois_elt, out, level, count, ws, ws_bytes, S(stream),
                      nullptr, true);
 }
@@ -352,26 +357,26 @@ int catfhe_wait_selftest(catfhe_ctx *ctx, uint64_t limit_ns, void *stream) {
 
 int catfhe_plain_import(catfhe_ctx *ctx, const int64_t *coeffs, uint32_t level, uint64_t *pt,
                         void *stream) {
-    if (!ctx || !coeffs || !pt) return CATFHE_EINVAL;
+    if (!ctx || !coeffs || !dev(pt)) return CATFHE_EINVAL;
     return op_plain_import(ctx->c, coeffs, level, pt, S(stream));
 }
 
 int catfhe_encode_ckks(catfhe_ctx *ctx, const double *slots, double scale, uint32_t level,
                        uint64_t *pt, void *ws, size_t ws_bytes, void *stream) {
-    if (!ctx || !slots || !pt) return CATFHE_EINVAL;
+    if (!ctx || !slots || !dev(pt)) return CATFHE_EINVAL;
     return op_encode_ckks(ctx->c, slots, scale, level, pt, ws, ws_bytes, S(stream));
 }
 
 int catfhe_decode_ckks(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *ct,
                        uint32_t level, double scale, double *slots, void *ws, size_t ws_bytes,
                        void *stream) {
-    if (!keys_ok(ctx, keys) || !ct || !slots) return CATFHE_EINVAL;
+    if (!keys_ok(ctx, keys) || !dev(ct) || !slots) return CATFHE_EINVAL;
     return op_decode_ckks(ctx->c, *keys->k, ct, level, scale, slots, ws, ws_bytes, S(stream));
 }
 
 int catfhe_mul_plain(catfhe_ctx *ctx, const uint64_t *a, const uint64_t *pt, uint64_t *out,
                      uint32_t level, uint32_t count, void *stream) {
-    if (!ctx || !a || !pt || !out) return CATFHE_EINVAL;
+    if (!ctx || !dev(a) || !dev(pt) || !dev(out)) return CATFHE_EINVAL;
     return op_mul_plain(ctx->c, a, pt, out, level, count, S(stream));
 }
 
@@ -379,38 +384,38 @@ int catfhe_rotate_hoisted(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64
                           const uint64_t *galois_elts, uint32_t n_rot, uint64_t *out,
                           uint32_t level, uint32_t count, void *ws, size_t ws_bytes,
                           void *stream) {
-    if (!keys_ok(ctx, keys) || !a || (n_rot > 0 && !out)) return CATFHE_EINVAL;
+    if (!keys_ok(ctx, keys) || !dev(a) || (n_rot > 0 && !dev(out))) return CATFHE_EINVAL;
     return op_rotate_hoisted(ctx->c, *keys->k, a, galois_elts, n_rot, out, level, count, ws,
                              ws_bytes, S(stream));
 }
 
 int catfhe_rescale(catfhe_ctx *ctx, const uint64_t *a, uint64_t *out, uint32_t level,
                    uint32_t count, void *ws, size_t ws_bytes, void *stream) {
-    if (!ctx || !a) return CATFHE_EINVAL;
+    if (!ctx || !dev(a)) return CATFHE_EINVAL;
     if (ctx->c.scheme == CATFHE_BFV) return CATFHE_ESCHEME;
     if (level < 2 || int(level) > ctx->c.L) return CATFHE_ELEVEL;
-    if (!out) return CATFHE_EINVAL;
+    if (!dev(out)) return CATFHE_EINVAL;
     return op_rescale(ctx->c, a, out, level, count, ws, ws_bytes, S(stream));
 }
 
 int catfhe_rescale_noalloc(catfhe_ctx *ctx, const uint64_t *a, uint64_t *out, uint32_t level,
                            uint32_t count, void *stream) {
-    if (!ctx || !a) return CATFHE_EINVAL;
+    if (!ctx || !dev(a)) return CATFHE_EINVAL;
     if (ctx->c.scheme == CATFHE_BFV) return CATFHE_ESCHEME;
     if (level < 2 || int(level) > ctx->c.L) return CATFHE_ELEVEL;
-    if (!out) return CATFHE_EINVAL;
+    if (!dev(out)) return CATFHE_EINVAL;
     return op_rescale_noalloc_impl(ctx->c, a, out, level, count, S(stream));
 }
 
 int catfhe_decrypt(catfhe_ctx *ctx, const catfhe_keys *keys, const uint64_t *ct, uint32_t level,
                    uint64_t factor, int64_t *msg, void *ws, size_t ws_bytes, void *stream) {
-    if (!keys_ok(ctx, keys) || !ct || !msg) return CATFHE_EINVAL;
+    if (!keys_ok(ctx, keys) || !dev(ct) || !msg) return CATFHE_EINVAL;
     return op_decrypt(ctx->c, *keys->k, ct, level, factor, msg, ws, ws_bytes, S(stream));
 }
 
 int catfhe_ntt(catfhe_ctx *ctx, uint64_t *limbs, uint32_t level, uint32_t count, int inverse,
                void *stream) {
-    if (!ctx || !limbs) return CATFHE_EINVAL;
+    if (!ctx || !dev(limbs)) return CATFHE_EINVAL;
     return op_ntt(ctx->c, limbs, level, count, inverse, S(stream));
 }
 

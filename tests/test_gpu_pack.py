@@ -93,3 +93,27 @@ def test_misaligned_workspace_is_refused_before_any_launch():
     assert e.value.code == -1
     torch.cuda.synchronize()
     assert bool((out == 7).all())
+
+
+def test_misaligned_ciphertext_buffers_are_refused():
+    """Ciphertext buffers must be 16-byte aligned (kernels move 16-byte words):
+    a view that starts one word into an allocation is refused with EINVAL by
+    single calls and by batch entries, before anything is enqueued."""
+    ctx = api.Context(MIXED)
+    keys = ctx.keygen(W.seed_for("pack-align"))
+    a = ctx.ct_uniform(W.seed_for("pack-align"), 0, 4)
+    flat = torch.empty(a.numel() + 2, dtype=torch.int64, device="cuda")
+    shifted = flat[1:1 + a.numel()].view(a.shape)
+    shifted.copy_(a)
+    out = torch.full_like(a, 7)
+    for call in (lambda: ctx.mul_relin(keys, shifted, a, out),
+                 lambda: ctx.add(shifted, a, out),
+                 lambda: ctx.rescale(shifted, out[:, :, :3].contiguous())):
+        with pytest.raises(api.CatfheError) as e:
+            call()
+        assert e.value.code == -1
+    with pytest.raises(api.CatfheError) as e:
+        api.run_batch([api.make_op(api.OP_ADD, ctx, shifted, out, b=a)], lanes=1)
+    assert e.value.code == -1
+    torch.cuda.synchronize()
+    assert bool((out == 7).all())
