@@ -349,7 +349,9 @@ int catfhe_rescale(catfhe_ctx *ctx, const uint64_t *a, uint64_t *out, uint32_t l
  * array and it keeps the last call's contents (nothing in it needs to start
  * at zero); calls whose device work overlaps race on it, so order them on
  * one stream.  Inputs and outputs are caller-owned device buffers as for
- * catfhe_rescale; `out` must not alias `a`. */
+ * catfhe_rescale; `out` must not overlap `a` (EINVAL, nothing enqueued).
+ * The context's device must be the caller's current device (EINVAL
+ * otherwise): the array has a different address on every GPU. */
 int catfhe_rescale_noalloc(catfhe_ctx *ctx, const uint64_t *a, uint64_t *out, uint32_t level,
                            uint32_t count, void *stream);
 

@@ -403,7 +403,7 @@ int catfhe_rescale_noalloc(catfhe_ctx *ctx, const uint64_t *a, uint64_t *out, ui
     if (!ctx || !dev(a)) return CATFHE_EINVAL;
     if (ctx->c.scheme == CATFHE_BFV) return CATFHE_ESCHEME;
     if (level < 2 || int(level) > ctx->c.L) return CATFHE_ELEVEL;
-    if (!dev(out)) return CATFHE_EINVAL;
+    if (!dev(out) || out == a) return CATFHE_EINVAL;
     return op_rescale_noalloc_impl(ctx->c, a, out, level, count, S(stream));
 }
 

@@ -34,10 +34,14 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 static std::mutex g_noalloc_mu;
 static void *g_noalloc_ptr[64];  // device address of the array, per device
 
-// Device address of the static scratch on the current device (looked up once).
-static int noalloc_scratch(void **out) {
+// Device address of the static scratch on the context's device (looked up
+// once per device).  The array's address differs per device, so the caller's
+// current device must be the context's: otherwise the kernels would get
+// another GPU's array with no error, and the call is refused instead.
+static int noalloc_scratch(const Context &c, void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return CATFHE_ECUDA;
+    if (dev != c.device) return CATFHE_EINVAL;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
         void *p = nullptr;
@@ -48,9 +52,22 @@ static int noalloc_scratch(void **out) {
     return CATFHE_OK;
 }
 
-size_t noalloc_bytes_needed(const Context &c, uint32_t level, uint32_t count) {
-    const size_t limbs = size_t(count) * 2 * (1 + (level >= 1 ? level - 1 : 0));
-    return kNoallocPlanBytes + limbs * c.n * 8;
+// Layout of the scratch for count ciphertexts at `level`: the plan, then the
+// inverse-transformed last limbs [count][2][N], then the lift
+// [count][2][level-1][N].  The size check and the call use these same
+// offsets, so the check covers every word the kernels touch:
+// 16 KiB + 16 count level N bytes in all.
+struct NoallocLayout {
+    size_t last_off, lift_off, end;
+};
+
+static NoallocLayout noalloc_layout(const Context &c, uint32_t level, uint32_t count) {
+    NoallocLayout l;
+    const size_t lo = level >= 1 ? level - 1 : 0;
+    l.last_off = kNoallocPlanBytes;
+    l.lift_off = l.last_off + size_t(count) * 2 * c.n * 8;
+    l.end = l.lift_off + size_t(count) * 2 * lo * c.n * 8;
+    return l;
 }
 
 // The rescale plan (one source prime q_{l-1}, targets q_0 .. q_{l-2}) in the
@@ -96,15 +113,23 @@ int op_rescale_noalloc_impl(Context &c, const uint64_t *a, uint64_t *out, uint32
     if (c.scheme == CATFHE_BFV) return CATFHE_ESCHEME;
     if (level < 2 || int(level) > c.L) return CATFHE_ELEVEL;
     if (count == 0) return CATFHE_OK;
-    if (noalloc_bytes_needed(c, level, count) > kNoallocBytes) return CATFHE_EWORKSPACE;
+    const NoallocLayout lay = noalloc_layout(c, level, count);
+    if (lay.end > kNoallocBytes) return CATFHE_EWORKSPACE;
+    // the combine reads a with a stride of 2 level N words and writes out with
+    // 2 (level-1) N: overlapping spans would overwrite inputs before they are read
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(a), o0 = reinterpret_cast<uintptr_t>(out);
+    const size_t a_bytes = size_t(count) * 2 * level * c.n * 8;
+    const size_t o_bytes = size_t(count) * 2 * (level - 1) * c.n * 8;
+    if (a0 < o0 + o_bytes && o0 < a0 + a_bytes) return CATFHE_EINVAL;
     void *base = nullptr;
-    int rc = noalloc_scratch(&base);
+    int rc = noalloc_scratch(c, &base);
     if (rc) return rc;
     const size_t n = c.n;
     const int lvl = int(level), lo = lvl - 1;
-    uint64_t *plan = static_cast<uint64_t *>(base);
-    uint64_t *last = reinterpret_cast<uint64_t *>(static_cast<char *>(base) + kNoallocPlanBytes);
-    uint64_t *lift = last + size_t(count) * 2 * n;
+    char *b8 = static_cast<char *>(base);
+    uint64_t *plan = reinterpret_cast<uint64_t *>(b8);
+    uint64_t *last = reinterpret_cast<uint64_t *>(b8 + lay.last_off);
+    uint64_t *lift = reinterpret_cast<uint64_t *>(b8 + lay.lift_off);
 
     uint64_t hplan[1 + 1 + 32 + 2 + 64 + 2 + 32 + 32];
     const size_t words = rescale_plan(c, level, hplan);

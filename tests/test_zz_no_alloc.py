@@ -41,15 +41,34 @@ def test_noalloc_rescale_equals_rescale_twice(name):
 
 
 def test_noalloc_full_size_and_limit():
+    """N = 2^16: the scratch holds 16 KiB + 16 count level N bytes of at most
+    32 MiB, so count * level <= 31.  Calls at the limit run and equal
+    catfhe_rescale; calls one step past it are refused before any launch."""
     ctx = api.Context(W.PRESETS["ckks_n16"])
-    a = _uniform(ctx, "noalloc-n16", 24, 1)
-    out = ctx.empty_ct(1, 23)
-    for _ in range(2):
-        got = ctx.export_ct(ctx.rescale_noalloc(a, out))
-        assert np.array_equal(got, ctx.export_ct(ctx.rescale(a)))
-    # two N = 2^16 ciphertexts at level 24 exceed the static scratch: refused
-    # before any work is enqueued
     lib = api.load()
-    rc = lib.catfhe_rescale_noalloc(ctx._h, ctypes.c_void_p(a.data_ptr()),
-                                    ctypes.c_void_p(out.data_ptr()), 24, 2, None)
-    assert rc == -7  # CATFHE_EWORKSPACE
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    for count, level in ((1, 24), (2, 15)):
+        a = _uniform(ctx, f"noalloc-n16-{count}", level, count)
+        out = ctx.empty_ct(count, level - 1)
+        for _ in range(2):
+            got = ctx.export_ct(ctx.rescale_noalloc(a, out))
+            assert np.array_equal(got, ctx.export_ct(ctx.rescale(a))), (count, level)
+    a = _uniform(ctx, "noalloc-n16-big", 24, 2)
+    out = ctx.empty_ct(2, 23)
+    keep = out.clone()
+    for count, level in ((2, 16), (3, 11), (2, 24)):
+        rc = lib.catfhe_rescale_noalloc(ctx._h, P(a), P(out), level, count, None)
+        assert rc == -7, (count, level)  # CATFHE_EWORKSPACE
+    torch.cuda.synchronize()
+    assert torch.equal(out, keep)        # nothing was written
+
+
+def test_noalloc_refuses_overlap():
+    """The output may not overlap the input: in place, or shifted by a limb."""
+    ctx = api.Context(W.PRESETS["ckks_n12"])
+    lib = api.load()
+    a = _uniform(ctx, "noalloc-overlap", 3, 2)
+    P = lambda p: ctypes.c_void_p(p)
+    base = a.data_ptr()
+    assert lib.catfhe_rescale_noalloc(ctx._h, P(base), P(base), 3, 2, None) == -1
+    assert lib.catfhe_rescale_noalloc(ctx._h, P(base), P(base + 8 * ctx.n), 3, 2, None) == -1
