@@ -170,7 +170,8 @@ def test_uneven_mix_full_sizes_sampled():
     """The uneven mix at its real sizes (N from 2^13 to 2^16 on one prime
     chain, levels 2..24, HMult+relin / HRotate / rescale, tuned NTT schedules,
     one captured graph over 8 lanes), 48 operations: every output equals the
-    single call, and two N = 2^13 outputs equal the oracle."""
+    single call, two N = 2^13 key-switching outputs and every rescale entry
+    (all four ring degrees) equal the oracle."""
     base = W.PRESETS["ckks_n16"]
     rng = W.rng_for("mix-test")
     ctxs = {}
@@ -227,3 +228,17 @@ def test_uneven_mix_full_sizes_sampled():
         assert np.array_equal(c.export_ct(o)[0], want), (kind, level)
         checked += 1
     assert checked == 2
+    # every rescale entry against the oracle's round(c / q_{l-1})
+    octxs, seen = {}, set()
+    for (log_n, level, kind, i, g, a, b), o in zip(meta, outs):
+        if kind != api.OP_RESCALE:
+            continue
+        pr, c, k, gs = ctxs[log_n]
+        if log_n not in octxs:
+            octxs[log_n] = oracle.Context(pr.scheme, pr.log_n, pr.q_bits, pr.p_bits, pr.dnum,
+                                          log_n_max=16)
+        oc = octxs[log_n]
+        want = oc.rescale(oc.ct_uniform(seed, 2 * i, level))
+        assert np.array_equal(c.export_ct(o)[0], want), (log_n, level)
+        seen.add(log_n)
+    assert seen == {13, 14, 15, 16}
