@@ -46,6 +46,8 @@ def parse():
                     help="skip the rotation and N=2^14 BFV/BGV side measurements")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the private-query serving sweep")
+    ap.add_argument("--detail", default=os.path.join(ROOT, "gpurun_out", "bench_detail.json"),
+                    help="where the full measurement record (sweeps, schedule tables) goes")
     return ap.parse_args()
 
 
@@ -117,76 +119,106 @@ class Clocks:
                 "samples": len(rows)}
 
 
+# ---------------------------------------------------------------- workload description
+
+def workload_config(world: int = 1) -> dict:
+    """The `config` object of both arms' lines (the same workload)."""
+    return {"workload": "ckks_n16: CKKS N=2^16 L=24 (50-bit q) K=4 (60-bit p) dnum=3, "
+                        "batch of 8 uniform ciphertext pairs, fused HMult+relin+rescale",
+            "N": 1 << 16, "L": 24, "K": 4, "dnum": 3, "batch": BATCH,
+            "l2": "inputs 384 MiB + key 84 MiB per step, larger than L2; no flush",
+            "parallelism": f"replicas x{world}"}
+
+
 # ---------------------------------------------------------------- CPU oracle leg
 
-def oracle_op_seconds(n_ops: int = 1, warm: int = 0):
-    """Times the CPU oracle on `n_ops` HMult+relin+rescale of the workload
-    (one ciphertext pair each), single-threaded, after `warm` untimed ones;
-    keygen untimed."""
+def _oracle_setup():
     import oracle
     from paper_2503_22227_gb300 import workloads as W
     p = W.PRESETS[PRESET]
     ctx = oracle.Context(p.scheme, p.log_n, p.q_bits, p.p_bits, p.dnum, log_n_max=p.log_n_max)
     keys = ctx.keygen(W.seed_for("bench-keys"))
-    seed = W.seed_for("bench-inputs")
-    times = []
-    for i in range(warm + n_ops):
-        a = ctx.ct_uniform(seed, 2 * i, p.L)
-        b = ctx.ct_uniform(seed, 2 * i + 1, p.L)
-        t0 = time.perf_counter()
-        ctx.rescale(ctx.mul_relin(keys, a, b))
-        if i >= warm:
-            times.append(time.perf_counter() - t0)
-    return times
+    return ctx, keys, W.seed_for("bench-inputs"), p
 
 
-def _ref_worker(args):
-    idx, n_ops, warm = args
-    return oracle_op_seconds(n_ops, warm)
+def _oracle_op(ctx, keys, seed, p, pair):
+    """One HMult+relin+rescale of uniform pair `pair` of the workload; seconds."""
+    a = ctx.ct_uniform(seed, 2 * pair, p.L)
+    b = ctx.ct_uniform(seed, 2 * pair + 1, p.L)
+    t0 = time.perf_counter()
+    ctx.rescale(ctx.mul_relin(keys, a, b))
+    return time.perf_counter() - t0
+
+
+def oracle_single_op_seconds() -> float:
+    """The oracle on one thread, one operation alone (keygen untimed)."""
+    ctx, keys, seed, p = _oracle_setup()
+    return _oracle_op(ctx, keys, seed, p, 0)
+
+
+def _ref_proc(first, n_ops, warm, barrier, q):
+    """One worker: keygen and `warm` untimed ops, then a barrier shared by all
+    workers, then `n_ops` timed ops on pairs first, first+1, ...; reports
+    (wall-clock start, end, per-op seconds)."""
+    ctx, keys, seed, p = _oracle_setup()
+    for i in range(warm):
+        _oracle_op(ctx, keys, seed, p, 100000 + first + i)
+    barrier.wait()
+    t_start = time.time()
+    times = [_oracle_op(ctx, keys, seed, p, first + i) for i in range(n_ops)]
+    q.put((first, t_start, time.time(), times))
 
 
 def oracle_pool(k: int, warm: int = 0):
-    """k oracle operations spread over min(k, cores) spawned processes (a
-    spawned pool: safe after CUDA has been initialised in this process),
-    each process first running ceil(warm / processes) untimed ones.
-    Returns (ops/s from the slowest worker's op time, processes, wall s,
-    s per op, warm-up ops run)."""
+    """k timed oracle operations over min(k, cores) spawned processes (safe
+    after CUDA has been initialised in this process), after `warm` untimed
+    ones spread over the same processes.  All processes start their timed
+    operations together (a barrier); the timed region runs from that start
+    to the last process's end.  Returns (ops/s over the region, processes,
+    region seconds, seconds per op on one core)."""
     import multiprocessing as mp
     cores = os.cpu_count() or 1
     procs = max(1, min(k, cores))
     per = [k // procs + (1 if i < k % procs else 0) for i in range(procs)]
-    w = -(-warm // procs) if warm > 0 else 0
-    t0 = time.perf_counter()
-    with mp.get_context("spawn").Pool(procs) as pool:
-        results = pool.map(_ref_worker, [(i, per[i], w) for i in range(procs)])
-    wall = time.perf_counter() - t0
-    busy = max(sum(r) for r in results)
-    return k / busy, procs, wall, busy / max(per), w * procs
+    wper = [warm // procs + (1 if i < warm % procs else 0) for i in range(procs)]
+    ctx = mp.get_context("spawn")
+    barrier, q = ctx.Barrier(procs), ctx.Queue()
+    firsts = [sum(per[:i]) for i in range(procs)]
+    ps = [ctx.Process(target=_ref_proc, args=(firsts[i], per[i], wper[i], barrier, q))
+          for i in range(procs)]
+    for pr in ps:
+        pr.start()
+    res = [q.get() for _ in ps]
+    for pr in ps:
+        pr.join()
+    t0 = min(r[1] for r in res)
+    t1 = max(r[2] for r in res)
+    per_op = statistics.median([t for r in res for t in r[3]])
+    return k / (t1 - t0), procs, t1 - t0, per_op
 
 
 def run_reference(args):
     """The CPU oracle on this host's cores: each step is one HMult+relin+
-    rescale of one pair; steps are spread over worker processes (spawned)."""
+    rescale of one ciphertext pair of the workload (a bounded sample of the
+    batched step); steps run in parallel over worker processes.  Rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     cores = os.cpu_count() or 1
-    # one operation per step, at most two per core, so the run stays bounded
-    k = max(1, min(args.steps, 2 * cores))
-    value, procs, wall, per_op, warmed = oracle_pool(k, args.warmup)
+    # at most four operations per core (about a minute), so the run stays bounded
+    k = max(1, min(args.steps, 4 * cores))
+    w = max(0, args.warmup)
+    value, procs, region, per_op = oracle_pool(k, w)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-        "n_gpus": args.gpus, "steps": k, "warmup": warmed, "ms_per_step": 1e3 * per_op,
+        "n_gpus": args.gpus, "steps": k, "warmup": w, "ms_per_step": 1e3 * region / k,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic",
-        "config": {"workload": "ckks_n16: CKKS N=2^16 L=24 K=4 dnum=3, HMult+relin+rescale "
-                               "of uniform ciphertext pairs", "N": 1 << 16, "L": 24, "K": 4,
-                   "dnum": 3},
+        "data": "synthetic", "config": workload_config(args.gpus),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
-                         "sample": f"{k} HMult+relin+rescale ops (one pair each; steps capped at "
-                                   f"2 per core) over {procs} processes, after {warmed} untimed "
-                                   f"warm-up ops (one or more per process); keygen untimed; "
-                                   f"wall {wall:.1f}s"},
+                         "sample": f"{k} HMult+relin+rescale ops of the workload, one ciphertext "
+                                   f"pair each (a step = one op), over {procs} processes started "
+                                   f"together after {w} untimed warm-up ops; keygen untimed; "
+                                   f"timed region {region:.1f}s; {per_op:.1f}s per op on one core"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -264,7 +296,7 @@ def uneven_mix(api, W, R, mm_peak, n_ops=256, lanes=8, reps=5):
     return {"value": n_ops / t, "unit": "ops/s", "n_ops": n_ops, "lanes": lanes,
             "graph_nodes": nodes, "ms_per_graph": t * 1e3,
             "one_lane_ops_per_s": n_ops / res[1][0],
-            "modmul_frac_of_peak": work / t / mm_peak,
+            "frac": work / t / mm_peak,
             "ntt_schedules": {f"2^{k}": {cls: {"chosen": cv[0], "us_per_schedule": cv[1]}
                                          for cls, cv in v.items()}
                               for k, v in tuned.items()},
@@ -272,28 +304,38 @@ def uneven_mix(api, W, R, mm_peak, n_ops=256, lanes=8, reps=5):
                     "frac = sum of per-op modular products / (time x modmul peak)"}
 
 
-def secondary(ctx, keys, a, api, W):
-    """HRotate by r = 1..16 on the batch of 8 (one Galois key each), and
-    HMult+relin on 16 pairs of the N=2^14 BFV and BGV chains."""
+def secondary(ctx, keys, a, api, W, R, mm_peak, hbm):
+    """HRotate by r = 1..16 on the batch of 8 (one Galois key each), the same
+    rotations hoisted, and HMult+relin on 16 pairs of the N=2^14 BFV and BGV
+    chains; each with its roofline fraction (the slower of algorithmic bytes
+    over HBM and algorithmic modular products over the measured modmul peak,
+    divided by the measured time per operation)."""
     import torch
-    out = {}
+    out, det = {}, {}
     gs = [ctx.galois_elt(r) for r in range(1, 17)]
     for g in gs:
         keys.gen_galois(g)
     rot = ctx.empty_ct(*a.shape[:1], a.shape[2])
+    n, L, K, alpha, batch = ctx.n, a.shape[2], ctx.K, ctx.alpha, a.shape[0]
+
+    def frac(work, nbytes, t_op):
+        return max(nbytes / hbm, work.modmuls / mm_peak) / t_op
 
     def rotate_all():
         for g in gs:
             ctx.rotate(keys, a, g, rot)
-    t = _time(rotate_all, 5)
-    out["hrotate_r1_16"] = {"value": a.shape[0] * len(gs) / t, "unit": "HRotate/s",
-                            "note": "8 ciphertexts at level 24, r = 1..16 (16 Galois keys)"}
+    t = _time(rotate_all, 5) / (batch * len(gs))
+    rb = R.bytes_keyswitch(n, L, L, 1, L, K, alpha, batch)
+    out["hrotate_r1_16"] = {"value": 1 / t, "unit": "HRotate/s",
+                            "frac": frac(R.ckks_rotate(n, L, K, alpha), rb, t)}
     hoisted = torch.empty((len(gs),) + tuple(a.shape), dtype=a.dtype, device=a.device)
-    th = _time(lambda: ctx.rotate_hoisted(keys, a, gs, hoisted), 5)
+    th = _time(lambda: ctx.rotate_hoisted(keys, a, gs, hoisted), 5) / (batch * len(gs))
+    hb = R.bytes_keyswitch(n, L, L, 1, L, K, alpha, batch, inputs_shared=len(gs))
     out["hrotate_r1_16_hoisted"] = {
-        "value": a.shape[0] * len(gs) / th, "unit": "HRotate/s",
-        "note": "the same 128 rotations with one shared ModUp per ciphertext "
-                "(catfhe_rotate_hoisted; outputs equal catfhe_rotate bit for bit)"}
+        "value": 1 / th, "unit": "HRotate/s",
+        "frac": frac(R.ckks_rotate_hoisted(n, L, K, alpha, len(gs)), hb, th)}
+    det["rotations"] = "8 ciphertexts at level 24, r = 1..16 (16 Galois keys); hoisted: one " \
+                       "shared ModUp per ciphertext (catfhe_rotate_hoisted)"
     for name in ("bfv_n14", "bgv_n14"):
         p = W.PRESETS[name]
         c2 = api.Context(p)
@@ -302,11 +344,18 @@ def secondary(ctx, keys, a, api, W):
         x = torch.cat([c2.ct_uniform(seed, 2 * i, p.L) for i in range(p.batch)])
         y = torch.cat([c2.ct_uniform(seed, 2 * i + 1, p.L) for i in range(p.batch)])
         o = c2.empty_ct(p.batch, p.L)
-        t = _time(lambda: c2.mul_relin(k2, x, y, o), 10)
-        out[name] = {"value": p.batch / t, "unit": "HMult+relin/s",
+        t = _time(lambda: c2.mul_relin(k2, x, y, o), 10) / p.batch
+        if p.scheme == W.BFV:
+            w = R.bfv_mul_relin(c2.n, p.L, c2.K, c2.alpha, c2.nb)
+        else:
+            w = R.bgv_mul_relin(c2.n, p.L, c2.K, c2.alpha)
+        nbytes = R.bytes_keyswitch(c2.n, p.L, p.L, 2, p.L, c2.K, c2.alpha, p.batch)
+        out[name] = {"value": 1 / t, "unit": "HMult+relin/s", "frac": frac(w, nbytes, t)}
+        det[name] = {"modmuls_per_op": w.modmuls, "bytes_per_op": nbytes,
                      "note": f"N=2^14, 8 x 55-bit q, t=65537, batch {p.batch}"}
         del c2, k2
-    return out
+    return out, det
+
 
 def serving_sweep(W, fracs=(0.1, 0.5, 0.8, 1.5), lanes=8, max_active=64):
     """The private-query workload (1000 x 4 encrypted table, N=2^16, L=24,
@@ -404,6 +453,98 @@ def ntt_traffic():
         return None
 
 
+def e2e_leg(ctx, keys, a, b, out, K, world, api, np, torch):
+    """End to end through the public API with host buffers.  Every step:
+    upload both input batches from page-locked host memory in coefficient
+    form (catfhe_ct_import: copy, then NTT on the device), HMult+relin+
+    rescale, and read the result batch back to page-locked host memory in
+    coefficient form (catfhe_ct_export: INTT on the device, then copy); all
+    asynchronous on three streams (uploads, compute, downloads) over two
+    buffer sets, so step k+1's upload and step k-1's download overlap step
+    k's compute.  Every step's copies and transforms are in the timed
+    region.  The link bound runs the same pipeline with the compute left out
+    (uploads and downloads only, same calls, same overlap), so it is the
+    rate the transfers alone allow."""
+    L = a.shape[2]
+    lo = out.shape[2]
+    BATCHn = a.shape[0]
+    ha = [torch.empty(a.shape, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+    hb = [torch.empty(b.shape, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+    coeff_a = ctx.export_ct(a)
+    coeff_b = ctx.export_ct(b)
+    for k in range(2):
+        ha[k].numpy().view(np.uint64)[...] = coeff_a
+        hb[k].numpy().view(np.uint64)[...] = coeff_b
+    ctx.mul_relin_rescale(keys, a, b, out)
+    ref = ctx.export_ct(out)
+    ho = [torch.empty(out.shape, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+    da = [torch.empty_like(a) for _ in range(2)]
+    db = [torch.empty_like(b) for _ in range(2)]
+    do = [torch.empty_like(out) for _ in range(2)]
+    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_cmp = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+    form_in = api.FORM_COEFF | api.FORM_ASYNC
+    form_out = api.FORM_COEFF | api.FORM_ASYNC
+    # every export runs on s_out in order, so one workspace serves both sets
+    with torch.cuda.stream(s_out):
+        ws_out = ctx.workspace(api.OP_EXPORT, lo, BATCHn)
+
+    def run(steps, compute=True):
+        for e in ev_cmp + ev_out:
+            e.record()
+        for i in range(steps):
+            k = i % 2
+            with torch.cuda.stream(s_in):
+                s_in.wait_event(ev_cmp[k])
+                ctx.import_ct(ha[k], form_in, out=da[k])
+                ctx.import_ct(hb[k], form_in, out=db[k])
+                ev_in[k].record(s_in)
+            with torch.cuda.stream(s_cmp):
+                s_cmp.wait_event(ev_in[k])
+                s_cmp.wait_event(ev_out[k])
+                if compute:
+                    ctx.mul_relin_rescale(keys, da[k], db[k], do[k])
+                ev_cmp[k].record(s_cmp)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(ev_cmp[k])
+                ctx.export_into(do[k], ho[k], form_out, ws=ws_out)
+                ev_out[k].record(s_out)
+        torch.cuda.synchronize()
+
+    run(3)
+    run(3, compute=False)
+    ke = max(3, K // 3)
+    from paper_2503_22227_gb300 import replicas
+    barrier(world)
+    t0 = time.perf_counter()
+    run(ke)
+    te = max_over_ranks(time.perf_counter() - t0, world)
+    got = [ho[k].numpy().view(np.uint64) for k in range((ke - 1) % 2, (ke - 1) % 2 + 1)]
+    if not np.array_equal(got[0], ref):
+        raise RuntimeError("end-to-end result differs from the device-resident result")
+    t_link = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        run(ke, compute=False)
+        t_link.append((time.perf_counter() - t1) / ke)
+    tl = min(t_link)
+    h2d = 2 * a.numel() * 8
+    d2h = out.numel() * 8
+    return {"value": world * BATCHn * ke / te, "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": te / ke * 1e3,
+            "note": "pinned host in/out, coefficient-form u64 limbs, catfhe_ct_import / "
+                    "catfhe_ct_export (asynchronous, NTT / INTT on the device) around "
+                    "catfhe_mul_relin_rescale, pipelined over 2 buffer sets and 3 streams; "
+                    "the last result is checked against the device-resident one",
+            "link": {"bound_per_s": BATCHn / tl, "ms_per_step": tl * 1e3,
+                     "gbs": (h2d + d2h) / tl / 1e9,
+                     "note": "the same pipeline without the compute"}}
+
+
 def run_catfhe(args):
     import numpy as np
     import torch
@@ -498,170 +639,80 @@ def run_catfhe(args):
     except OSError:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0)) * 1e9
+    issue = R.issue_bounds(float((clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)))
     work = R.ckks_mul_relin_rescale(p.n, L, p.K, ctx.alpha)
     bytes_op = R.bytes_mul_relin_rescale(p.n, L, L, p.K, ctx.alpha, BATCH)
     t_roof = max(bytes_op / hbm, work.modmuls / mm_peak)
     t_meas = total_s / (BATCH * K) * world
+    t_roof_issue = max(bytes_op / hbm, work.modmuls / issue["modmul_per_s"])
 
-    # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        # Every step: upload both input batches from pinned host memory,
-        # HMult+relin+rescale, copy the result batch back to pinned host
-        # memory, all through the C ABI.  Steps are pipelined over two buffer
-        # sets and three streams (uploads, compute, downloads), so step k+1's
-        # upload and step k-1's download overlap step k's compute; every
-        # step's copies stay inside the timed region.
-        ha = torch.empty(a.shape, dtype=torch.int64, pin_memory=True)
-        hb = torch.empty(b.shape, dtype=torch.int64, pin_memory=True)
-        ha.copy_(a.cpu())
-        hb.copy_(b.cpu())
-        ref = out.cpu()
-        # the client's ciphertexts in the bit-packed transfer form (50-bit
-        # fields), packed once on the host before the timed region
-        pa, pb = ctx.pack(ha).pin_memory(), ctx.pack(hb).pin_memory()
-        lo = out.shape[2]
-        wo = ctx.packed_words(lo, BATCH)
-        hpo = [torch.empty(wo, dtype=torch.int64, pin_memory=True) for _ in range(2)]
-        da = [torch.empty_like(a) for _ in range(2)]
-        db = [torch.empty_like(b) for _ in range(2)]
-        do = [torch.empty_like(out) for _ in range(2)]
-        sa = [torch.empty(pa.numel(), dtype=torch.int64, device="cuda") for _ in range(2)]
-        sb = [torch.empty(pb.numel(), dtype=torch.int64, device="cuda") for _ in range(2)]
-        so = [torch.empty(wo, dtype=torch.int64, device="cuda") for _ in range(2)]
-        s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-        ev_in = [torch.cuda.Event() for _ in range(2)]
-        ev_cmp = [torch.cuda.Event() for _ in range(2)]
-        ev_out = [torch.cuda.Event() for _ in range(2)]
-        asyn = api.FORM_ASYNC
+        e2e = e2e_leg(ctx, keys, a, b, out, K, world, api, np, torch)
 
-        def upload(k):
-            ctx.import_packed(pa, L, BATCH, out=da[k], ws=sa[k], flags=asyn)
-            ctx.import_packed(pb, L, BATCH, out=db[k], ws=sb[k], flags=asyn)
-
-        def download(k):
-            ctx.export_packed(do[k], hpo[k], ws=so[k], flags=asyn)
-
-        def e2e_run(steps):
-            for e in ev_cmp + ev_out:
-                e.record()
-            for i in range(steps):
-                k = i % 2
-                with torch.cuda.stream(s_in):
-                    s_in.wait_event(ev_cmp[k])
-                    upload(k)
-                    ev_in[k].record(s_in)
-                with torch.cuda.stream(s_cmp):
-                    s_cmp.wait_event(ev_in[k])
-                    s_cmp.wait_event(ev_out[k])
-                    ctx.mul_relin_rescale(keys, da[k], db[k], do[k])
-                    ev_cmp[k].record(s_cmp)
-                with torch.cuda.stream(s_out):
-                    s_out.wait_event(ev_cmp[k])
-                    download(k)
-                    ev_out[k].record(s_out)
-            torch.cuda.synchronize()
-
-        # the host link's own rates, through the same calls: uploads alone,
-        # downloads alone, both at once (two streams)
-        def link_s(up, down, reps=5):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(reps):
-                if up:
-                    with torch.cuda.stream(s_in):
-                        upload(0)
-                if down:
-                    with torch.cuda.stream(s_out):
-                        download(1)
-            torch.cuda.synchronize()
-            return (time.perf_counter() - t0) / reps
-
-        h2d_b, d2h_b = (pa.numel() + pb.numel()) * 8, wo * 8
-        link_s(True, True, 2)
-        t_up, t_down, t_both = link_s(True, False), link_s(False, True), link_s(True, True)
-        link = {"h2d_gbs": h2d_b / t_up / 1e9, "d2h_gbs": d2h_b / t_down / 1e9,
-                "both_gbs": (h2d_b + d2h_b) / t_both / 1e9,
-                "bound_per_s": BATCH / t_both,
-                "note": "one step's packed uploads and download alone and at once, through "
-                        "the same calls (unpack / pack kernels included); bound_per_s = "
-                        "operations per second if a step took only its transfers"}
-        e2e_run(3)
-        ke = max(3, K // 3)
-        barrier(world)
-        t0 = time.perf_counter()
-        e2e_run(ke)
-        te = max_over_ranks(time.perf_counter() - t0, world)
-        last = ctx.unpack(hpo[(ke - 1) % 2].numpy().view(np.uint64), BATCH, lo)
-        if not np.array_equal(last, ref.numpy().view(np.uint64)):
-            raise RuntimeError("end-to-end result differs from the device-resident result")
-        e2e = {"value": world * BATCH * ke / te, "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d_b), "d2h_bytes_per_step": int(d2h_b),
-               "note": "pinned host in/out in the bit-packed transfer form (50-bit fields; the "
-                       "client packs its inputs once before timing) through "
-                       "catfhe_ct_import_packed / catfhe_ct_export_packed (asynchronous), "
-                       "pipelined over 2 buffer sets and 3 streams; the last result is "
-                       "unpacked and checked against the device-resident result",
-               "link": link}
-
+    detail = {}
     side = None
     if not args.no_secondary:
-        side = secondary(ctx, keys, a, api, W)
-        side["uneven_mix"] = uneven_mix(api, W, R, mm_peak)
+        side, sdet = secondary(ctx, keys, a, api, W, R, mm_peak, hbm)
+        detail["secondary"] = sdet
+        mix = uneven_mix(api, W, R, mm_peak)
+        detail["uneven_mix"] = mix
+        side["uneven_mix"] = {k: mix[k] for k in ("value", "unit", "n_ops", "frac")}
+        side["uneven_mix"]["schedules_timed_2^16"] = [len(v["us_per_schedule"])
+                                                       for v in mix["ntt_schedules"]["2^16"].values()]
     serving = None
     if not args.no_serving:
         serving = serving_sweep(W)
+        detail["serving"] = serving
     if rank != 0:
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         # the oracle as it stands on every host core (one op per process),
-        # and on one thread
-        pv, procs, wall, _, _ = oracle_pool(os.cpu_count() or 1)
-        ts = oracle_op_seconds(1)
+        # and one op alone on one thread
+        pv, procs, region, _ = oracle_pool(os.cpu_count() or 1)
+        ts = oracle_single_op_seconds()
         cpu = {"value": pv, "unit": UNIT, "cores": procs, "kind": "oracle",
-               "sample": f"{procs} HMult+relin+rescale ops of the workload (N=2^16, L=24; one "
-                         f"uniform pair each), one per spawned process on {procs} cores; "
-                         f"keygen untimed; wall {wall:.1f}s",
-               "single_thread": {"value": 1.0 / ts[0], "cores": 1,
-                                 "sample": "1 op of the same workload on one thread"}}
+               "sample": f"{procs} HMult+relin+rescale ops of the workload, one per spawned "
+                         f"process on {procs} cores, {region:.1f}s; one op alone on one "
+                         f"thread {ts:.1f}s ({1.0 / ts:.3f} op/s)"}
     step_ms_sorted = sorted(step_ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": max(3, args.warmup), "ms_per_step": 1e3 * total_s / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic",
-        "config": {"workload": "ckks_n16: CKKS N=2^16 L=24 (50-bit q) K=4 (60-bit p) dnum=3, "
-                               "batch of 8 uniform ciphertext pairs, fused HMult+relin+rescale",
-                   "N": p.n, "L": L, "K": p.K, "dnum": p.dnum, "batch": BATCH,
-                   "l2": "inputs 384 MiB + key 84 MiB per step, larger than L2; no flush",
-                   "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "kernel": "batched forward NTT (k_ntt_fwd_cols + k_ntt_fwd_rows)",
-                     "achieved": ntt_rate / 1e9, "peak": bf_peak / 1e9, "unit": "Gbutterfly/s",
-                     "frac": ntt_rate / bf_peak, "traffic": ntt_traffic(),
-                     "peak_source": "measured: register-resident loop of the forward "
-                                    "butterfly the transform runs on these 50-bit primes "
-                                    "(catfhe_measure_int_peak, wide form), whole GPU",
-                     "peak_narrow_form": bf_narrow_peak / 1e9,
-                     "hbm_view": {"achieved_gbs": ntt_gbs, "peak_gbs": hbm / 1e9,
-                                  "frac": ntt_gbs * 1e9 / hbm},
-                     "limbs_per_launch": n_limbs, "us_per_launch": ntt_s * 1e6},
-        "step_roofline": {"modmuls_per_op": work.modmuls, "bytes_per_op": bytes_op,
-                          "modmul_peak_per_s": mm_peak, "hbm_bytes_per_s": hbm,
-                          "roofline_us_per_op": t_roof * 1e6, "measured_us_per_op": t_meas * 1e6,
-                          "frac": t_roof / t_meas},
-        "single": {"value": single_value, "unit": UNIT,
-                   "note": "same 8 pairs as 8 single-ciphertext launches"},
-        "latency_ms": {"p50": step_ms_sorted[len(step_ms) // 2],
-                       "p99": step_ms_sorted[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],
-                       "unit": "ms per batched step of 8"},
-        "gpu_launches": int(launches),
+        "data": "synthetic", "config": workload_config(world),
+        "single": {"value": single_value, "batched_over_single": value / world / single_value},
         "p99_ms": serving["p99_ms"] if serving else None,
-        "serving": serving,
-        "secondary": side,
+        "p50_ms": serving["p50_ms"] if serving else None,
+        "roofline": {"bound": "alu", "kernel": "fwd NTT k_ntt_fwd_cols+k_ntt_fwd_rows, 384 limbs",
+                     "achieved": round(ntt_rate / 1e9, 1), "peak": round(bf_peak / 1e9, 1),
+                     "unit": "Gbutterfly/s", "frac": ntt_rate / bf_peak, "traffic": ntt_traffic(),
+                     "frac_of_issue_bound": ntt_rate / issue["butterfly_wide_per_s"],
+                     "us": round(ntt_s * 1e6, 1), "hbm_frac": ntt_gbs * 1e9 / hbm},
+        "step_roofline": {"frac": t_roof / t_meas, "frac_of_issue_bound": t_roof_issue / t_meas,
+                          "us_per_op": round(t_meas * 1e6, 2),
+                          "roof_us_per_op": round(t_roof * 1e6, 2),
+                          "modmul_peak": mm_peak},
+        "latency_ms": {"p50": step_ms_sorted[len(step_ms) // 2],
+                       "p99": step_ms_sorted[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},
+        "gpu_launches": int(launches),
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+        "secondary": side,
+        "serving": ({"saturation_per_s": serving["saturation_per_s"],
+                     "at_offered_per_s": serving["at_offered_per_s"]} if serving else None),
     }
-    print(json.dumps(line), flush=True)
+    detail["line"] = line
+    detail["step_roofline"] = {"modmuls_per_op": work.modmuls, "bytes_per_op": bytes_op,
+                               "hbm_bytes_per_s": hbm, "issue_bounds": issue,
+                               "butterfly_narrow_peak": bf_narrow_peak}
+    try:
+        os.makedirs(os.path.dirname(args.detail), exist_ok=True)
+        with open(args.detail, "w") as f:
+            json.dump(detail, f, indent=1)
+    except OSError:
+        pass
+    print(json.dumps(line, separators=(",", ":")), flush=True)
 
 
 def main():

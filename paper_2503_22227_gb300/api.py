@@ -281,10 +281,12 @@ class Context:
         del keep
         return out
 
-    def export_into(self, ct, host, form: int = FORM_NATIVE):
-        """Device ciphertexts -> a (pinned) CPU int64 tensor of the same shape."""
+    def export_into(self, ct, host, form: int = FORM_NATIVE, ws=None):
+        """Device ciphertexts -> a (pinned) CPU int64 tensor of the same shape
+        (ws: a workspace from workspace(OP_EXPORT, level, count), or None)."""
         count, _, level, _ = ct.shape
-        ws = self.workspace(OP_EXPORT, level, count)
+        if ws is None:
+            ws = self.workspace(OP_EXPORT, level, count)
         _check(load().catfhe_ct_export(self._h, _ptr(ct), level, count, form,
                                        ctypes.c_void_p(host.data_ptr()), _ptr(ws), ws.numel(),
                                        _stream()), "catfhe_ct_export")
