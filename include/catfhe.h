@@ -59,7 +59,8 @@ enum {
     CATFHE_ENOMEM = -4,     /* device allocation failed                      */
     CATFHE_ECUDA = -5,      /* a CUDA call or kernel launch failed           */
     CATFHE_ESCHEME = -6,    /* operation not defined for this scheme         */
-    CATFHE_EWORKSPACE = -7  /* workspace smaller than required               */
+    CATFHE_EWORKSPACE = -7, /* workspace smaller than required               */
+    CATFHE_ETIMEOUT = -8    /* a kernel's bounded wait gave up (catfhe_sync)  */
 };
 
 enum { CATFHE_CKKS = 0, CATFHE_BFV = 1, CATFHE_BGV = 2 };
@@ -382,6 +383,15 @@ int catfhe_ntt(catfhe_ctx *ctx, uint64_t *limbs, uint32_t level, uint32_t count,
  * check that a timed-out wait ends and is reported. */
 int catfhe_device_status(catfhe_ctx *ctx, int32_t *flags, int clear, void *stream);
 int catfhe_wait_selftest(catfhe_ctx *ctx, uint64_t limit_ns, void *stream);
+
+/* Waits until everything enqueued on `stream` has finished (operations are
+ * stream-ordered and asynchronous; import/export without CATFHE_FORM_ASYNC,
+ * decrypt and decode synchronise by themselves).  Returns CATFHE_ECUDA if
+ * the stream reports an error, CATFHE_ETIMEOUT if any bounded wait of this
+ * context's kernels has given up since the status word was last cleared
+ * (any bit of catfhe_device_status, the self-test's included; the word is
+ * left as it is), else CATFHE_OK. */
+int catfhe_sync(catfhe_ctx *ctx, void *stream);
 
 /* Diagnostics.  catfhe_measure_int_peak times register-resident loops of
  * independent 64-bit Shoup products by a constant (fully reduced) and of

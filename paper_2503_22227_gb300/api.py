@@ -43,7 +43,7 @@ EXPORTS = [
     "catfhe_rotate_hoisted", "catfhe_plain_import", "catfhe_mul_plain",
     "catfhe_encode_ckks", "catfhe_decode_ckks", "catfhe_device_status", "catfhe_wait_selftest",
     "catfhe_packed_words", "catfhe_ct_import_packed", "catfhe_ct_export_packed",
-    "catfhe_pack_host", "catfhe_unpack_host",
+    "catfhe_pack_host", "catfhe_unpack_host", "catfhe_sync",
 ]
 
 
@@ -127,6 +127,7 @@ def load(path: str = LIB_PATH):
             "catfhe_measure_int_peak": (ctypes.c_int, [vp, vp, vp, vp]),
             "catfhe_kernel_launches": (u64, []),
             "catfhe_rescale_noalloc": (ctypes.c_int, [vp, vp, vp, u32, u32, vp]),
+            "catfhe_sync": (ctypes.c_int, [vp, vp]),
             "catfhe_batch_workspace_bytes": (sz, [vp, u32, u32]),
             "catfhe_run_batch": (ctypes.c_int, [vp, u32, u32, vp, sz, vp]),
             "catfhe_batch_capture": (ctypes.c_int, [vp, u32, u32, vp, sz, ctypes.POINTER(vp)]),
@@ -462,6 +463,11 @@ class Context:
         _check(load().catfhe_device_status(self._h, ctypes.byref(v), 1 if clear else 0, _stream()),
                "catfhe_device_status")
         return v.value
+
+    def sync(self) -> None:
+        """Waits for the current stream; raises CatfheError (ETIMEOUT) if a
+        bounded wait of this context's kernels has given up."""
+        _check(load().catfhe_sync(self._h, _stream()), "catfhe_sync")
 
     def wait_selftest(self, limit_ns: int = 20_000_000) -> None:
         _check(load().catfhe_wait_selftest(self._h, int(limit_ns), _stream()), "catfhe_wait_selftest")

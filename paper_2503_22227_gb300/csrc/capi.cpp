@@ -93,6 +93,7 @@ const char *catfhe_strerror(int code) {
         case CATFHE_ECUDA: return "CUDA error";
         case CATFHE_ESCHEME: return "operation not defined for this scheme";
         case CATFHE_EWORKSPACE: return "workspace too small";
+        case CATFHE_ETIMEOUT: return "a kernel's bounded wait timed out";
         default: return "unknown error";
     }
 }
@@ -348,6 +349,13 @@ int catfhe_device_status(catfhe_ctx *ctx, int32_t *flags, int clear, void *strea
     if (cudaStreamSynchronize(s) != cudaSuccess) return CATFHE_ECUDA;
     *flags = v;
     return CATFHE_OK;
+}
+
+int catfhe_sync(catfhe_ctx *ctx, void *stream) {
+    int32_t flags = 0;
+    const int rc = catfhe_device_status(ctx, &flags, 0, stream);
+    if (rc) return rc;
+    return flags ? CATFHE_ETIMEOUT : CATFHE_OK;
 }
 
 int catfhe_wait_selftest(catfhe_ctx *ctx, uint64_t limit_ns, void *stream) {

@@ -38,6 +38,9 @@ def test_strerror_and_null_arguments(lib):
     lib.catfhe_strerror.restype = ctypes.c_char_p
     assert lib.catfhe_strerror(0) == b"ok"
     assert lib.catfhe_strerror(-3) == b"key-switching key missing"
+    assert lib.catfhe_strerror(-8) == b"a kernel's bounded wait timed out"
+    lib.catfhe_sync.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.catfhe_sync(None, None) == -1
     # argument checks happen before any CUDA call
     lib.catfhe_ctx_create.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     assert lib.catfhe_ctx_create(None, None) == -1

@@ -28,8 +28,12 @@ def test_timed_out_wait_is_reported_and_context_survives():
     ctx.wait_selftest(20_000_000)            # 20 ms limit
     assert ctx.device_status(clear=False) == 2
     assert time.perf_counter() - t0 < 5.0
+    with pytest.raises(api.CatfheError) as e:   # catfhe_sync reports it, leaves the word
+        ctx.sync()
+    assert e.value.code == -8                # ETIMEOUT
     assert ctx.device_status() == 2          # read and clear
     assert ctx.device_status() == 0
+    ctx.sync()                               # clear word: OK
     # the context still computes the same result
     assert torch.equal(ctx.mul_relin(keys, a, b), want)
     assert ctx.device_status() == 0
