@@ -428,16 +428,26 @@ def serving_sweep(W, fracs=(0.1, 0.5, 0.8, 1.5), lanes=8, max_active=64):
 
 
 NTT_TRAFFIC = os.path.join(ROOT, "profiles", "ntt_fwd_ckks_n16_384limbs.md")
-NTT_SOURCE = os.path.join(ROOT, "paper_2503_22227_gb300", "csrc", "ntt.cu")
+NTT_SOURCES = [os.path.join(ROOT, "paper_2503_22227_gb300", "csrc", f)
+               for f in ("ntt.cu", "ntt_kernels.cuh", "ntt_part.cuh", "ntt_n16.cu",
+                         "butterfly.cuh", "modarith.cuh")]
+
+
+def ntt_source_sha() -> str:
+    """SHA-256 over the sources of the N = 2^16 transform's kernels."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in NTT_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
 
 
 def ntt_traffic():
     """DRAM bytes per forward transform of the 384 limbs (both passes), from
-    the committed ncu summary, if it was taken on the current NTT source."""
-    import hashlib
+    the committed ncu summary, if it was taken on the current NTT sources."""
     try:
         text = open(NTT_TRAFFIC).read()
-        src = hashlib.sha256(open(NTT_SOURCE, "rb").read()).hexdigest()
+        src = ntt_source_sha()
     except OSError:
         return None
     fields = {}
@@ -445,7 +455,7 @@ def ntt_traffic():
         if ":" in line and line.startswith("- "):
             k, v = line[2:].split(":", 1)
             fields[k.strip()] = v.strip().strip("`")
-    if fields.get("ntt.cu sha256") != src:
+    if fields.get("ntt sources sha256") != src:
         return None
     try:
         return int(fields["traffic bytes per transform"])

@@ -388,7 +388,100 @@ __device__ __forceinline__ uint64_t eval_split(const uint32_t (&al)[KMAX],
     return P.lazy ? r : csub(r, p);
 }
 
+// Two adjacent coefficients per thread: every plan constant read from shared
+// memory serves both coefficients' products (one load and one sum of halves
+// instead of two), and sources and results move as 16-byte words.
+template <int K>
+__device__ __forceinline__ bool mixed_radix_split_pair(const ulonglong2 (&r)[K], uint32_t (&al)[2][K],
+                                                       uint32_t (&ah)[2][K], bool (&gt)[2],
+                                                       const MontView &P) {
+    gt[0] = gt[1] = false;
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        Acc3 a0{0, 0, 0}, a1{0, 0, 0};
+        const uint64_t wd = ld_plan(&P.C[size_t(j) * K + j]);
+        mac3(a0, uint32_t(r[j].x) & kMask30, uint32_t(r[j].x >> 30), wd);
+        mac3(a1, uint32_t(r[j].y) & kMask30, uint32_t(r[j].y >> 30), wd);
+#pragma unroll
+        for (int i = 0; i < j; i++) {
+            const uint64_t w = ld_plan(&P.C[size_t(i) * K + j]);
+            mac3(a0, al[0][i], ah[0][i], w);
+            mac3(a1, al[1][i], ah[1][i], w);
+        }
+        const uint64_t mj = P.smod[2 * j], mq = P.smod[2 * j + 1];
+        const uint64_t a0j = csub(redc(join3(a0), mj, mq), mj);
+        const uint64_t a1j = csub(redc(join3(a1), mj, mq), mj);
+        al[0][j] = uint32_t(a0j) & kMask30;
+        ah[0][j] = uint32_t(a0j >> 30);
+        al[1][j] = uint32_t(a1j) & kMask30;
+        ah[1][j] = uint32_t(a1j >> 30);
+        const uint64_t hj = P.h[j];
+        if (a0j != hj) gt[0] = a0j > hj;
+        if (a1j != hj) gt[1] = a1j > hj;
+    }
+    return gt[0] || gt[1];
+}
+
+template <int K>
+__device__ __forceinline__ ulonglong2 eval_split_pair(const uint32_t (&al)[2][K],
+                                                      const uint32_t (&ah)[2][K],
+                                                      const bool (&gt)[2], const MontView &P,
+                                                      uint32_t t) {
+    Acc3 a0{0, 0, 0}, a1{0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < K; i++) {
+        const uint64_t w = P.Ct[size_t(i) * P.T + t];
+        mac3(a0, al[0][i], ah[0][i], w);
+        mac3(a1, al[1][i], ah[1][i], w);
+    }
+    const uint64_t mn = P.Mneg[t];
+    if (gt[0]) {  // below 2^60 each: ll stays below 2^64
+        a0.ll += mn;
+        a0.mm += mn;
+    }
+    if (gt[1]) {
+        a1.ll += mn;
+        a1.mm += mn;
+    }
+    const uint64_t p = P.dmod[2 * t], pi = P.dmod[2 * t + 1];
+    uint64_t r0 = redc(join3(a0), p, pi), r1 = redc(join3(a1), p, pi);
+    if (!P.lazy) {
+        r0 = csub(r0, p);
+        r1 = csub(r1, p);
+    }
+    return make_ulonglong2(r0, r1);
+}
+
 // ================================================================== kernels
+
+// Split-weight layout, every plan of the launch with exactly K sources, two
+// adjacent coefficients per thread (128 threads cover 256 coefficients).
+template <int K>
+__global__ void __launch_bounds__(128, 5)
+k_conv_pair(const PlanList plans, const uint64_t *__restrict__ src, size_t src_item,
+            size_t src_plan, uint64_t *__restrict__ dst, size_t dst_item, size_t dst_plan,
+            uint32_t log_n) {
+    grid_dep_wait();
+    extern __shared__ uint64_t splan[];
+    const uint64_t *gp = plans.p[blockIdx.z];
+    copy_plan(splan, gp, uint32_t(plan_words(gp[0])));
+    __syncthreads();
+    const size_t n = size_t(1) << log_n;
+    const uint64_t *s = src + blockIdx.y * src_item + blockIdx.z * src_plan;
+    uint64_t *d = dst + blockIdx.y * dst_item + blockIdx.z * dst_plan;
+    const MontView P = mont_view(splan);
+    const size_t x = 2 * (size_t(blockIdx.x) * blockDim.x + threadIdx.x);
+    if (x >= n) return;
+    ulonglong2 r[K];
+#pragma unroll
+    for (int i = 0; i < K; i++) r[i] = *reinterpret_cast<const ulonglong2 *>(s + P.src_off[i] * n + x);
+    uint32_t al[2][K], ah[2][K];
+    bool gt[2];
+    mixed_radix_split_pair<K>(r, al, ah, gt, P);
+    for (uint32_t t = 0; t < P.T; t++)
+        *reinterpret_cast<ulonglong2 *>(d + P.dst_off[t] * n + x) =
+            eval_split_pair<K>(al, ah, gt, P, t);
+}
 
 template <int KMAX>
 __device__ __forceinline__ void load_sources(uint64_t (&a)[KMAX], uint32_t k,
@@ -528,7 +621,24 @@ int launch_conv(const Context &c, const PlanList &plans, const uint64_t *src, si
     const size_t sm = size_t(plans.words) * 8;
     if (plans.split) {
         if (plans.kmax > 8) return CATFHE_EINVAL;
-        if (plans.kmin == plans.kmax) {
+        if (plans.kmin == plans.kmax && (reinterpret_cast<uintptr_t>(src) & 15) == 0 &&
+            (reinterpret_cast<uintptr_t>(dst) & 15) == 0 && (src_item | src_plan | dst_item |
+                                                              dst_plan) % 2 == 0 && n % 256 == 0) {
+            // one source count for every plan, 16-byte aligned sources and
+            // results: exact instantiation, two coefficients per thread
+            const dim3 g2(unsigned(n / 256), items, plans.n);
+            switch (plans.kmax) {
+#define PAIRK(K)                                                                               \
+    case K:                                                                                    \
+        launch_pdl(k_conv_pair<K>, g2, dim3(128), sm, s, plans, src, src_item, src_plan, dst,  \
+                   dst_item, dst_plan, c.log_n);                                               \
+        break;
+                PAIRK(1) PAIRK(2) PAIRK(3) PAIRK(4) PAIRK(5) PAIRK(6) PAIRK(7) PAIRK(8)
+#undef PAIRK
+                default:
+                    return CATFHE_EINVAL;
+            }
+        } else if (plans.kmin == plans.kmax) {
             // one source count for every plan: exact instantiation
             switch (plans.kmax) {
 #define EXACTK(K)                                                                              \

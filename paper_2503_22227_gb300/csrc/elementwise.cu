@@ -192,13 +192,20 @@ k_ip_stream(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
 // shared buffers, the next ciphertext's copies in flight while the threads
 // compute on the current one; all threads then read shared memory only.
 // Used when every address is 16-byte aligned (bulk-copy rule) and
-// BETA <= 4; same arithmetic as k_ip, bit for bit.
-constexpr uint32_t kIpTile = 512;
+// BETA <= 8; same arithmetic as k_ip, bit for bit.  Tiles of 512
+// coefficients (256 threads) up to 4 digits; 256 coefficients (128 threads)
+// for 5 to 8 digits, so that the 2 BETA key tiles and the two buffers
+// (72 KB at BETA = 8) leave room for 3 CTAs per SM.
+template <int BETA>
+struct IpTile {
+    static constexpr uint32_t value = BETA <= 4 ? 512 : 256;
+};
 
 template <int BETA>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(IpTile<BETA>::value / 2)
 k_ip_bulk(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n, uint32_t count) {
     grid_dep_wait();
+    constexpr uint32_t kIpTile = IpTile<BETA>::value;
     extern __shared__ __align__(128) uint64_t sm[];
     __shared__ __align__(8) uint64_t bars[3];  // buffer 0, buffer 1, keys
     const size_t n = size_t(1) << log_n;
@@ -319,24 +326,25 @@ static int launch_ip_regs(const Context &c, const IpArgs &a, uint32_t count, cud
 
 int launch_ip(const Context &c, const IpArgs &a, uint32_t count, cudaStream_t s) {
     const size_t n = c.n;
-    bool bulk = a.beta <= 4 && a.status != nullptr && n % kIpTile == 0 && aligned16(a.ext) &&
+    bool bulk = a.beta <= 8 && a.status != nullptr && n % 512 == 0 && aligned16(a.ext) &&
                 aligned16(a.key) && aligned16(a.y) && (!a.own || aligned16(a.own)) &&
                 (!a.add0 || aligned16(a.add0)) && (!a.add1 || aligned16(a.add1)) &&
                 (a.ext_item * 8) % 16 == 0 && (a.own_item * 8) % 16 == 0 &&
                 (a.add_item * 8) % 16 == 0 && (a.y_item * 8) % 16 == 0;
     if (bulk) {
-        const dim3 g(unsigned(n / kIpTile), a.M);
         switch (a.beta) {
 #define IPB(B)                                                                                   \
     case B: {                                                                                    \
-        const size_t smb = size_t(4 * B + 4) * kIpTile * 8;                                      \
+        constexpr uint32_t tile = IpTile<B>::value;                                              \
+        const size_t smb = size_t(4 * B + 4) * tile * 8;                                         \
         if (cudaFuncSetAttribute(k_ip_bulk<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                  int(smb)) != cudaSuccess)                                       \
             return CATFHE_ECUDA;                                                                 \
-        launch_pdl(k_ip_bulk<B>, g, dim3(256), smb, s, a, c.d_mods, c.log_n, count);             \
+        launch_pdl(k_ip_bulk<B>, dim3(unsigned(n / tile), a.M), dim3(tile / 2), smb, s, a,       \
+                   c.d_mods, c.log_n, count);                                                    \
         break;                                                                                   \
     }
-            IPB(1) IPB(2) IPB(3) IPB(4)
+            IPB(1) IPB(2) IPB(3) IPB(4) IPB(5) IPB(6) IPB(7) IPB(8)
 #undef IPB
             default: bulk = false;
         }

@@ -110,6 +110,7 @@ DevMod h_devmod(uint64_t q, uint64_t n, uint64_t psi) {
     uint64_t x = q;  // -q^-1 mod 2^64 by Newton's iteration (q odd)
     for (int i = 0; i < 6; i++) x *= 2 - q * x;
     m.qinv = 0 - x;
+    m.m64 = q > (uint64_t(1) << 33) ? (uint64_t)(((u128)1 << 64) / q) : 0;
     if (n) {
         m.ninv = h_invmod(n % q, q);
         m.ninv_s = h_shoup(m.ninv, q);

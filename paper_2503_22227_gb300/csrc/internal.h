@@ -28,7 +28,7 @@ struct DevMod {
     uint64_t ninv, ninv_s;    // N^-1 mod q
     uint64_t ninvw, ninvw_s;  // N^-1 * psi^-1(bitrev 1) mod q (last inverse stage)
     uint64_t qinv;            // -q^-1 mod 2^64 (Montgomery reduction)
-    uint64_t pad;
+    uint64_t m64;             // floor(2^64 / q) when q > 2^33 (fits 32 bits), else 0
 };
 
 // Addressing of a batch of limbs: limb l of a launch is entry r = l % period
@@ -194,6 +194,10 @@ int launch_unpack(const Context &c, const uint64_t *packed, uint64_t *out, uint3
 int launch_pack(const Context &c, const uint64_t *in, uint64_t *packed, uint32_t level,
                 uint32_t polys, cudaStream_t s);
 
+// Forward NTT whose outputs for primes below 2^57 are left unreduced (below
+// 68q; larger primes reduced to [0, q)), for a consumer that reduces anyway.
+int launch_ntt_fwd_lazy(const Context &c, const uint64_t *src, uint64_t *dst, const LimbMap &map,
+                        uint32_t n_limbs, cudaStream_t s);
 int launch_ntt_fwd_combine(const Context &c, uint64_t *lift, const LimbMap &map, uint32_t n_limbs,
                            const NttEpilogue &epi, cudaStream_t s);
 
