@@ -394,6 +394,15 @@ def serving_sweep(W, fracs=(0.1, 0.5, 0.8, 1.5), lanes=8, max_active=64):
         points.append({"offered_per_s": rate, "requests": count, "throughput_per_s": st.throughput,
                        **st.latency, "mean_active": st.mean_active, "max_active": st.max_active,
                        "joined_running_batch": st.admitted_while_busy, "ticks": st.ticks})
+    # the same offered load as the headline point, with ticks bounded to the
+    # 16 oldest active requests (oldest first) instead of all of them
+    half = fracs[1] if len(fracs) > 1 else fracs[0]
+    rate = half * mu
+    count = int(min(192, max(32, rate * 3.0)))
+    st = S.serve(S.make_requests(table, count, rate, f"serve-{half}"), eng, budget, max_active,
+                 max_batch=16)
+    oldest16 = {"offered_per_s": rate, "requests": count, "throughput_per_s": st.throughput,
+                **st.latency, "ticks": st.ticks}
     # search-and-average: circuit (sum and count) + two-party inverse + HMult,
     # one query at a time, wall time including the client's decrypt/encrypt
     import numpy as np
@@ -410,7 +419,7 @@ def serving_sweep(W, fracs=(0.1, 0.5, 0.8, 1.5), lanes=8, max_active=64):
     out = {"unit": "queries/s", "saturation_per_s": mu,
            "burst64": {"throughput_per_s": mu, **burst.latency, "ticks": burst.ticks},
            "profile": prof,
-           "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
+           "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "oldest16": oldest16,
            "at_offered_per_s": head["offered_per_s"], "sweep": points,
            "request": {"rows": S.ROWS, "columns": S.COLS, "stages": len(table.circuit.stages()),
                        "ops": {k: v for k, v in counts.items() if k != "input"},
@@ -546,13 +555,10 @@ def e2e_leg(ctx, keys, a, b, out, K, world, api, np, torch):
     return {"value": world * BATCHn * ke / te, "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": te / ke * 1e3,
-            "note": "pinned host in/out, coefficient-form u64 limbs, catfhe_ct_import / "
-                    "catfhe_ct_export (asynchronous, NTT / INTT on the device) around "
-                    "catfhe_mul_relin_rescale, pipelined over 2 buffer sets and 3 streams; "
-                    "the last result is checked against the device-resident one",
+            "note": "pinned coefficient-form u64 limbs through catfhe_ct_import/export "
+                    "around the step, every step",
             "link": {"bound_per_s": BATCHn / tl, "ms_per_step": tl * 1e3,
-                     "gbs": (h2d + d2h) / tl / 1e9,
-                     "note": "the same pipeline without the compute"}}
+                     "gbs": (h2d + d2h) / tl / 1e9}}
 
 
 def run_catfhe(args):
@@ -699,6 +705,7 @@ def run_catfhe(args):
                      "achieved": round(ntt_rate / 1e9, 1), "peak": round(bf_peak / 1e9, 1),
                      "unit": "Gbutterfly/s", "frac": ntt_rate / bf_peak, "traffic": ntt_traffic(),
                      "frac_of_issue_bound": ntt_rate / issue["butterfly_wide_per_s"],
+                     "frac_of_mul_pipe_bound": ntt_rate * R.LOOP_MUL_PIPE_BUSY / bf_peak,
                      "us": round(ntt_s * 1e6, 1), "hbm_frac": ntt_gbs * 1e9 / hbm},
         "step_roofline": {"frac": t_roof / t_meas, "frac_of_issue_bound": t_roof_issue / t_meas,
                           "us_per_op": round(t_meas * 1e6, 2),
@@ -713,9 +720,12 @@ def run_catfhe(args):
                      "at_offered_per_s": serving["at_offered_per_s"]} if serving else None),
     }
     detail["line"] = line
+    lo, hi, wide = api.measure_imad_rates()
     detail["step_roofline"] = {"modmuls_per_op": work.modmuls, "bytes_per_op": bytes_op,
                                "hbm_bytes_per_s": hbm, "issue_bounds": issue,
-                               "butterfly_narrow_peak": bf_narrow_peak}
+                               "butterfly_narrow_peak": bf_narrow_peak,
+                               "imad_rates_per_s": {"mad.lo.u32": lo, "mad.hi.u32": hi,
+                                                    "mad.wide.u32": wide}}
     try:
         os.makedirs(os.path.dirname(args.detail), exist_ok=True)
         with open(args.detail, "w") as f:

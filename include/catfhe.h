@@ -406,6 +406,16 @@ int catfhe_sync(catfhe_ctx *ctx, void *stream);
  * since it was loaded. */
 int catfhe_measure_int_peak(double *modmul_per_s, double *butterfly_per_s,
                             double *butterfly_wide_per_s, void *stream);
+/* The device's rates, over the whole GPU, of the three 32-bit multiply
+ * instructions the 64-bit modular arithmetic is made of: low product
+ * (mad.lo.u32), high product (mad.hi.u32) and widening product
+ * (mad.wide.u32), each in register-resident loops of independent chains,
+ * best of five launches, in instructions (thread operations) per second
+ * (any pointer may be NULL); `stream` is synchronised.  With how many of
+ * each a butterfly issues (a profiler's count), they bound the transform
+ * from the hardware side. */
+int catfhe_measure_imad_rates(double *lo_per_s, double *hi_per_s, double *wide_per_s,
+                              void *stream);
 uint64_t catfhe_kernel_launches(void);
 
 /* ---- Uneven batches (many independent operations in one submission) ----

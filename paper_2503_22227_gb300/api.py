@@ -43,7 +43,7 @@ EXPORTS = [
     "catfhe_rotate_hoisted", "catfhe_plain_import", "catfhe_mul_plain",
     "catfhe_encode_ckks", "catfhe_decode_ckks", "catfhe_device_status", "catfhe_wait_selftest",
     "catfhe_packed_words", "catfhe_ct_import_packed", "catfhe_ct_export_packed",
-    "catfhe_pack_host", "catfhe_unpack_host", "catfhe_sync",
+    "catfhe_pack_host", "catfhe_unpack_host", "catfhe_sync", "catfhe_measure_imad_rates",
 ]
 
 
@@ -125,6 +125,7 @@ def load(path: str = LIB_PATH):
             "catfhe_ntt": (ctypes.c_int, [vp, vp, u32, u32, ctypes.c_int, vp]),
             "catfhe_workspace_bytes": (sz, [vp, ctypes.c_int, u32, u32]),
             "catfhe_measure_int_peak": (ctypes.c_int, [vp, vp, vp, vp]),
+            "catfhe_measure_imad_rates": (ctypes.c_int, [vp, vp, vp, vp]),
             "catfhe_kernel_launches": (u64, []),
             "catfhe_rescale_noalloc": (ctypes.c_int, [vp, vp, vp, u32, u32, vp]),
             "catfhe_sync": (ctypes.c_int, [vp, vp]),
@@ -556,6 +557,14 @@ def measure_int_peak() -> tuple[float, float, float]:
                                           _stream()),
            "catfhe_measure_int_peak")
     return mm.value, bf.value, bw.value
+
+
+def measure_imad_rates() -> tuple[float, float, float]:
+    """(mad.lo.u32, mad.hi.u32, mad.wide.u32) thread instructions per second."""
+    lo, hi, wide = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().catfhe_measure_imad_rates(ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(wide),
+                                            _stream()), "catfhe_measure_imad_rates")
+    return lo.value, hi.value, wide.value
 
 
 def kernel_launches() -> int:

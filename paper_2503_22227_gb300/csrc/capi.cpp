@@ -62,6 +62,7 @@ int op_export_packed(Context &c, const uint64_t *ct, uint32_t level, uint32_t co
 size_t packed_words(const Context &c, uint32_t level);
 int op_decrypt(Context &c, const Keys &k, const uint64_t *ct, uint32_t level, uint64_t factor,
                int64_t *msg, void *ws, size_t ws_bytes_in, cudaStream_t s);
+int measure_imad_rates(double *lo_per_s, double *hi_per_s, double *wide_per_s, cudaStream_t s);
 int measure_int_peak(double *modmul_per_s, double *bfly_per_s, double *bfly_wide_per_s,
                      cudaStream_t s);
 int op_rescale_noalloc_impl(Context &c, const uint64_t *a, uint64_t *out, uint32_t level,
@@ -430,6 +431,11 @@ int catfhe_ntt(catfhe_ctx *ctx, uint64_t *limbs, uint32_t level, uint32_t count,
 int catfhe_measure_int_peak(double *modmul_per_s, double *butterfly_per_s,
                             double *butterfly_wide_per_s, void *stream) {
     return measure_int_peak(modmul_per_s, butterfly_per_s, butterfly_wide_per_s, S(stream));
+}
+
+int catfhe_measure_imad_rates(double *lo_per_s, double *hi_per_s, double *wide_per_s,
+                              void *stream) {
+    return measure_imad_rates(lo_per_s, hi_per_s, wide_per_s, S(stream));
 }
 
 uint64_t catfhe_kernel_launches(void) { return launches_total(); }

@@ -245,57 +245,12 @@ __device__ __forceinline__ uint64_t eval_mont(const uint64_t (&a)[KMAX], bool gt
 // ================================================================== split weights
 
 // Montgomery layout with k <= 8 and every modulus below 2^60: digits and
-// weights are split into 30-bit halves, x = xh 2^30 + xl, and a sum of
-// products is the value ll + mm 2^30 + hh 2^60 with
-//   ll = sum xl wl,  mm = sum (xl wh + xh wl),  hh = sum xh wh.
-// With at most 8 products per sum, ll and hh stay below 2^63 and mm below
-// 16 (2^30 - 1)^2 < 2^64.  The middle sum is formed by Karatsuba's identity:
-// the accumulators hold ll, kk = sum (xl + xh)(wl + wh) and hh, three
-// 32 x 32 -> 64-bit multiply-adds per product instead of four; kk may wrap
-// modulo 2^64, but mm = kk - ll - hh is below 2^64, so the difference taken
-// modulo 2^64 is mm exactly.  The joined value is the same exact sum as in
-// the Montgomery layout (below 2^64 times the modulus), reduced by one
-// Montgomery reduction.
+// weights are split into 30-bit halves (Acc3, mac3 and join3 in
+// modarith.cuh).  With at most 8 products per sum, ll and hh stay below
+// 2^63 and mm below 16 (2^30 - 1)^2 < 2^64.  The joined value is the same
+// exact sum as in the Montgomery layout (below 2^64 times the modulus),
+// reduced by one Montgomery reduction.
 
-struct Acc3 {
-    uint64_t ll, mm, hh;  // mm holds kk until join3
-};
-
-// Three 32 x 32 -> 64-bit multiply-adds, written as PTX mad.wide.u32 (the
-// four-product form in C++ measured slower than in PTX, 1788 vs 1743 us per
-// batched step; Karatsuba's three products: 1498 -> 1488 us).  The sums of
-// halves are below 2^31.
-__device__ __forceinline__ void mac3(Acc3 &a, uint32_t xl, uint32_t xh, uint64_t w) {
-    const uint32_t wl = uint32_t(w), wh = uint32_t(w >> 32);
-    asm("{\n\t.reg .u32 xs, ws;\n\t"
-        "add.u32 xs, %3, %4;\n\t"
-        "add.u32 ws, %5, %6;\n\t"
-        "mad.wide.u32 %0, %3, %5, %0;\n\t"
-        "mad.wide.u32 %1, xs, ws, %1;\n\t"
-        "mad.wide.u32 %2, %4, %6, %2;\n\t}"
-        : "+l"(a.ll), "+l"(a.mm), "+l"(a.hh)
-        : "r"(xl), "r"(xh), "r"(wl), "r"(wh));
-}
-
-// ll + mm 2^30 + hh 2^60 as 128 bits, mm recovered from kk first.  A term
-// added to ll after the products (the folded -M of the centring) is added to
-// kk too, so that the difference is unchanged.
-__device__ __forceinline__ U128 join3(const Acc3 &a0) {
-    Acc3 a = a0;
-    a.mm = a0.mm - a0.ll - a0.hh;
-    U128 x;
-    asm("add.cc.u64 %0, %2, %3;\n\t"
-        "addc.u64 %1, %4, 0;"
-        : "=l"(x.lo), "=l"(x.hi)
-        : "l"(a.ll), "l"(a.mm << 30), "l"(a.mm >> 34));
-    asm("add.cc.u64 %0, %0, %2;\n\t"
-        "addc.u64 %1, %1, %3;"
-        : "+l"(x.lo), "+l"(x.hi)
-        : "l"(a.hh << 60), "l"(a.hh >> 4));
-    return x;
-}
-
-constexpr uint32_t kMask30 = (1u << 30) - 1;
 
 // A plan constant read from shared memory at its point of use.  The load is
 // volatile so that the compiler keeps it there: with the exact-source-count

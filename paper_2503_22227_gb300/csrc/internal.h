@@ -19,6 +19,9 @@ constexpr int kMapMax = 128;      // limbs per group in one LimbMap
 constexpr int kGatherMax = 8;
 constexpr int kConvMaxK = 32;     // sources of one exact base conversion
 constexpr int kConvMaxT = 48;     // targets of one exact base conversion
+// Bound, in multiples of q, of the forward NTT's unreduced words for primes
+// below 2^57 (inputs below 4q, 4q more per stage over at most 16 stages).
+constexpr uint64_t kWideWordsQ = 68;
 
 // One modulus as the kernels see it.  q < 2^62.
 struct DevMod {

@@ -114,6 +114,61 @@ __device__ __forceinline__ uint64_t redc(U128 acc, uint64_t q, uint64_t qinv) {
     return acc.hi + mulhi(u, q) + (acc.lo != 0 ? 1 : 0);
 }
 
+// ------------------------------------------------------------ split products
+// Sums of products of words below 2^60, each split into 30-bit halves
+// x = xh 2^30 + xl: the sum is ll + mm 2^30 + hh 2^60 with
+//   ll = sum xl wl,  mm = sum (xl wh + xh wl),  hh = sum xh wh.
+// The middle sum is formed by Karatsuba's identity: the accumulators hold
+// ll, kk = sum (xl + xh)(wl + wh) and hh, three 32 x 32 -> 64-bit
+// multiply-adds per product; kk may wrap modulo 2^64, but when mm is below
+// 2^64 (the caller's bound) the difference kk - ll - hh taken modulo 2^64 is
+// mm exactly.  A widening multiply-add occupies the integer multiply pipe
+// as long as a 32-bit high product, so three of them cost less than the
+// four low and four high products of mac() (measured per instruction on
+// GB300: 2 pipe cycles per 32-bit low product, 4 per high or widening one).
+// The conversions use them; in the HBM-bound inner product and tensor the
+// extra splitting and joining measured slower (inner product 162 -> 172 us,
+// tensor 122 -> 123 us per batched step).
+struct Acc3 {
+    uint64_t ll, mm, hh;  // mm holds kk until join3
+};
+
+// Three 32 x 32 -> 64-bit multiply-adds, written as PTX mad.wide.u32 (the
+// four-product form in C++ measured slower than in PTX, 1788 vs 1743 us per
+// batched step; Karatsuba's three products: 1498 -> 1488 us).  The sums of
+// halves are below 2^31.
+__device__ __forceinline__ void mac3(Acc3 &a, uint32_t xl, uint32_t xh, uint64_t w) {
+    const uint32_t wl = uint32_t(w), wh = uint32_t(w >> 32);
+    asm("{\n\t.reg .u32 xs, ws;\n\t"
+        "add.u32 xs, %3, %4;\n\t"
+        "add.u32 ws, %5, %6;\n\t"
+        "mad.wide.u32 %0, %3, %5, %0;\n\t"
+        "mad.wide.u32 %1, xs, ws, %1;\n\t"
+        "mad.wide.u32 %2, %4, %6, %2;\n\t}"
+        : "+l"(a.ll), "+l"(a.mm), "+l"(a.hh)
+        : "r"(xl), "r"(xh), "r"(wl), "r"(wh));
+}
+
+// ll + mm 2^30 + hh 2^60 as 128 bits, mm recovered from kk first.  A term
+// added to ll after the products (the folded -M of the centring) is added to
+// kk too, so that the difference is unchanged.
+__device__ __forceinline__ U128 join3(const Acc3 &a0) {
+    Acc3 a = a0;
+    a.mm = a0.mm - a0.ll - a0.hh;
+    U128 x;
+    asm("add.cc.u64 %0, %2, %3;\n\t"
+        "addc.u64 %1, %4, 0;"
+        : "=l"(x.lo), "=l"(x.hi)
+        : "l"(a.ll), "l"(a.mm << 30), "l"(a.mm >> 34));
+    asm("add.cc.u64 %0, %0, %2;\n\t"
+        "addc.u64 %1, %1, %3;"
+        : "+l"(x.lo), "+l"(x.hi)
+        : "l"(a.hh << 60), "l"(a.hh >> 4));
+    return x;
+}
+
+constexpr uint32_t kMask30 = (1u << 30) - 1;
+
 // a*b mod q for a, b < 2^64 (exact).
 __device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, const DevMod &m) {
     U128 x{a * b, mulhi(a, b)};

@@ -65,9 +65,6 @@ __device__ __forceinline__ uint64_t reduce_fwd(uint64_t x, const DevMod &m) {
     return m.m64 ? reduce_fast(x, m.q, uint32_t(m.m64)) : reduce_any(x, m);
 }
 
-// Bound of the forward transform's unreduced words for primes under 2^57
-// (inputs below 4q, 4q more per stage over at most 16 stages).
-constexpr uint64_t kWideWordsQ = 68;
 
 // Limb of this CTA: group g (ciphertext or polynomial) and position r within
 // the map's period.  PRIME_MAJOR (used by the forward transform, where it

@@ -141,6 +141,24 @@ static int modup(Context &c, const uint64_t *d2c, uint64_t *ext, uint32_t count,
                        count, s);
 }
 
+// Whether the lifted digits' forward NTT may leave its words unreduced: the
+// inner product is their only reader and reduces its sums once (Montgomery,
+// valid below 2^64 q); with words below 68q from an unreduced transform, its
+// beta products and the folded P d term stay below (68 beta + 1) q^2.  Used
+// when that bound holds for every prime below 2^57 of Q_l u P (larger
+// primes are reduced anyway).
+static bool ext_lazy(const Context &c, int level) {
+    const int beta = (level + c.alpha - 1) / c.alpha;
+    for (int i = 0; i < level + c.K; i++) {
+        const uint64_t q = c.mod(ext_prime(c, level, i));
+        if (q < (uint64_t(1) << 57) &&
+            (unsigned __int128)(kWideWordsQ * uint64_t(beta) + 1) * q >=
+                ((unsigned __int128)1 << 64))
+            return false;
+    }
+    return true;
+}
+
 // NTT of the lifted limbs of ext (all positions if own_too).
 static int ntt_ext(Context &c, uint64_t *ext, uint32_t count, int level, bool own_too,
                    cudaStream_t s) {
@@ -159,20 +177,8 @@ static int ntt_ext(Context &c, uint64_t *ext, uint32_t count, int level, bool ow
     }
     m.period = e;
     m.src_stride = m.dst_stride = uint32_t(beta * M);
-    // The inner product is the only reader of these limbs and reduces its
-    // sums once (Montgomery, valid below 2^64 q): with words below 68q from
-    // an unreduced transform, its beta products and the folded P d term stay
-    // below (68 beta + 1) q^2.  Unreduced outputs are used when that bound
-    // holds for every prime below 2^57 (larger primes are reduced anyway).
-    bool lazy = true;
-    for (uint32_t i = 0; i < e; i++) {
-        const uint64_t q = c.mod(m.prime[i]);
-        if (q < (uint64_t(1) << 57) && (unsigned __int128)(68 * uint64_t(beta) + 1) * q >=
-                                           ((unsigned __int128)1 << 64))
-            lazy = false;
-    }
-    return lazy ? launch_ntt_fwd_lazy(c, ext, ext, m, e * count, s)
-                : launch_ntt_fwd(c, ext, ext, m, e * count, s);
+    return ext_lazy(c, level) ? launch_ntt_fwd_lazy(c, ext, ext, m, e * count, s)
+                              : launch_ntt_fwd(c, ext, ext, m, e * count, s);
 }
 
 static int inner_product(Context &c, const uint64_t *ext, const uint64_t *own, const uint64_t *key,

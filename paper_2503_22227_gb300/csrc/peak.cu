@@ -61,13 +61,52 @@ __global__ void __launch_bounds__(256) k_peak_bfly(uint64_t *out, uint64_t q, ui
     out[tid] = acc;
 }
 
+// Rates of the single 32-bit multiply instructions the 64-bit arithmetic is
+// built from, each in 8 independent chains per thread: the low product
+// (mad.lo), the high product (mad.hi) and the widening product (mad.wide,
+// whose 32-bit operand is the chain's own low word, so the loop issues no
+// shift).  Their ratios are the multiply pipe's occupancy per instruction;
+// with the counts of each kind per butterfly they bound the transform.
+template <int KIND>
+__global__ void __launch_bounds__(256) k_peak_imad(uint64_t *out, uint32_t c, int iters) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t x[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; j++) x[j] = tid * 7u + j + 0x80000000u;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int j = 0; j < kChains; j++) {
+            if (KIND == 0) {
+                uint32_t r;
+                asm volatile("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(uint32_t(x[j])), "r"(c), "r"(uint32_t(j)));
+                x[j] = r;
+            } else if (KIND == 1) {
+                uint32_t r;
+                asm volatile("mad.hi.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(uint32_t(x[j])), "r"(c), "r"(uint32_t(x[j])));
+                x[j] = r;
+            } else {
+                uint64_t r;
+                asm volatile("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(uint32_t(x[j])), "r"(c), "l"(x[j]));
+                x[j] = r;
+            }
+        }
+    }
+    uint64_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < kChains; j++) acc ^= x[j];
+    out[tid] = acc;
+}
+
 // Best of `reps` launches, in operations per second.
 static int time_kernel(int which, cudaStream_t s, double *rate) {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CATFHE_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return CATFHE_ECUDA;
-    const void *fn = which == 2   ? (const void *)k_peak_bfly<true>
+    const void *fn = which == 5   ? (const void *)k_peak_imad<2>
+                     : which == 4 ? (const void *)k_peak_imad<1>
+                     : which == 3 ? (const void *)k_peak_imad<0>
+                     : which == 2 ? (const void *)k_peak_bfly<true>
                      : which == 1 ? (const void *)k_peak_bfly<false>
                                   : (const void *)k_peak_modmul;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess)
@@ -88,7 +127,13 @@ static int time_kernel(int which, cudaStream_t s, double *rate) {
     int rc = CATFHE_OK;
     for (int rep = 0; rep < 6 && rc == CATFHE_OK; rep++) {
         cudaEventRecord(e0, s);
-        if (which == 2)
+        if (which == 5)
+            k_peak_imad<2><<<blocks, 256, 0, s>>>(out, 0x9E3779B1u, iters);
+        else if (which == 4)
+            k_peak_imad<1><<<blocks, 256, 0, s>>>(out, 0x9E3779B1u, iters);
+        else if (which == 3)
+            k_peak_imad<0><<<blocks, 256, 0, s>>>(out, 0x9E3779B1u, iters);
+        else if (which == 2)
             k_peak_bfly<true><<<blocks, 256, 0, s>>>(out, q, w, ws, iters);
         else if (which == 1)
             k_peak_bfly<false><<<blocks, 256, 0, s>>>(out, q, w, ws, iters);
@@ -114,6 +159,14 @@ int measure_int_peak(double *modmul_per_s, double *bfly_per_s, double *bfly_wide
     if (modmul_per_s) rc = time_kernel(0, s, modmul_per_s);
     if (rc == CATFHE_OK && bfly_per_s) rc = time_kernel(1, s, bfly_per_s);
     if (rc == CATFHE_OK && bfly_wide_per_s) rc = time_kernel(2, s, bfly_wide_per_s);
+    return rc;
+}
+
+int measure_imad_rates(double *lo_per_s, double *hi_per_s, double *wide_per_s, cudaStream_t s) {
+    int rc = CATFHE_OK;
+    if (lo_per_s) rc = time_kernel(3, s, lo_per_s);
+    if (rc == CATFHE_OK && hi_per_s) rc = time_kernel(4, s, hi_per_s);
+    if (rc == CATFHE_OK && wide_per_s) rc = time_kernel(5, s, wide_per_s);
     return rc;
 }
 

@@ -134,6 +134,15 @@ INSTR_PER_BUTTERFLY = 28.5
 INSTR_PER_BUTTERFLY_WIDE = 21.0
 
 
+# The integer multiply pipe (ncu: fmaheavy) is the one the arithmetic fills:
+# a 32-bit low product occupies it 2 cycles per warp instruction, a high or
+# widening product 4 (catfhe_measure_imad_rates, and ncu's pipe counters on
+# those loops).  ncu puts the wide-butterfly loop of catfhe_measure_int_peak
+# at this fraction of the pipe's cycles, so its rate divided by this is the
+# rate of that butterfly with the pipe busy on every cycle.
+LOOP_MUL_PIPE_BUSY = 0.927
+
+
 def issue_bounds(sm_mhz: float) -> dict:
     """Operations per second if the loops issued an instruction on every
     scheduler cycle at `sm_mhz`."""

@@ -115,8 +115,11 @@ class Admission:
 
 
 def serve(requests: list, engine, budget_bytes: int, max_active: int = 64, depth: int = 2,
-          clock=time.perf_counter, idle=None) -> ServeStats:
+          clock=time.perf_counter, idle=None, max_batch: int | None = None) -> ServeStats:
     """Runs `requests` (sorted by arrival) to completion; see the module text.
+
+    max_batch: at most this many active requests advance per tick, the
+    oldest first (None: every active request advances every tick).
 
     engine protocol:
       need(req) -> bytes          device memory the request reserves
@@ -180,11 +183,12 @@ def serve(requests: list, engine, budget_bytes: int, max_active: int = 64, depth
             engine.wait(token)
             retire(token, done)
             continue
-        engine.submit(engine.stage(active))
+        batch = active if max_batch is None else active[:max_batch]
+        engine.submit(engine.stage(batch))
         ticks += 1
         act_sum += len(active)
         max_act = max(max_act, len(active))
-        done = [r for r in active if engine.is_done(r)]
+        done = [r for r in batch if engine.is_done(r)]
         if done:
             active = [r for r in active if not engine.is_done(r)]
         for r in done:

@@ -212,6 +212,23 @@ def test_serve_completes_all_and_batches_continuously():
         assert e1.results[r.id] == eng.results[r.id]
 
 
+def test_oldest_first_batches_are_bounded_and_exact():
+    """max_batch = 3: no tick carries more than 3 requests, each tick takes
+    the oldest active ones, and every result equals the unbounded run's."""
+    arr = np.linspace(0, 0.004, 12)
+    eng = FakeEngine(stages=5)
+    st = S.serve(_reqs(arr), eng, budget_bytes=10 ** 9, max_active=16, clock=eng.clock,
+                 idle=eng.idle, max_batch=3)
+    assert st.served == 12 and len(eng.results) == 12
+    assert all(len(b) <= 3 for b in eng.batches)
+    for b in eng.batches:
+        ids = [i for i, _ in b]
+        assert ids == sorted(ids)
+    ref = FakeEngine(stages=5)
+    S.serve(_reqs(arr), ref, budget_bytes=10 ** 9, max_active=16, clock=ref.clock, idle=ref.idle)
+    assert eng.results == ref.results
+
+
 def test_admission_respects_budget_and_slots():
     eng = FakeEngine(stages=4, need=300)
     reqs = _reqs(np.zeros(20))
