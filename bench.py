@@ -578,6 +578,11 @@ def run_catfhe(args):
     b = torch.cat([ctx.ct_uniform(seed, 2 * i + 1, L) for i in range(BATCH)])
     out = ctx.empty_ct(BATCH, L - 1)
     stream = torch.cuda.current_stream()
+    # the NTT schedule of each launch size class this workload uses, picked by
+    # the library's tuner (the step's transforms run on 40 to 240 limbs per
+    # half batch; the roofline's on 384)
+    tuned = {"<=64": ctx.tune_ntt(2 * L), "<=256": ctx.tune_ntt(4 * L),
+             ">256": ctx.tune_ntt(2 * BATCH * L)}
 
     def step():
         ctx.mul_relin_rescale(keys, a, b, out)
@@ -720,6 +725,8 @@ def run_catfhe(args):
                      "at_offered_per_s": serving["at_offered_per_s"]} if serving else None),
     }
     detail["line"] = line
+    detail["ntt_schedules_headline"] = {k: {"chosen": v[0], "us_per_schedule": v[1]}
+                                        for k, v in tuned.items()}
     lo, hi, wide = api.measure_imad_rates()
     detail["step_roofline"] = {"modmuls_per_op": work.modmuls, "bytes_per_op": bytes_op,
                                "hbm_bytes_per_s": hbm, "issue_bounds": issue,

@@ -95,6 +95,18 @@ __device__ __forceinline__ uint32_t hi_bits(uint32_t tau, int v, int sh) {
 
 // ------------------------------------------------------------------ forward
 
+// Twiddles a thread needs in the stages after a row pass's exchange, when
+// there are at most 16 of them (else 0: they are read at their use).
+template <int LOGR, int LOGE>
+struct PrefetchCount {
+    static constexpr int count() {
+        int c = 0;
+        for (int st = LOGE; st < LOGR; st++) c += (LOGR - st) >= LOGE ? 1 : ((1 << LOGE) >> (LOGR - st));
+        return c;
+    }
+    static constexpr int value = count() <= 16 ? count() : 0;
+};
+
 template <int LOGR, int LOGE, int NT, bool WIDE>
 __device__ __forceinline__ void fwd_cols_body(uint64_t (&x)[1 << LOGE], uint64_t *sm,
                                               const ulonglong2 *w, uint64_t q, int cl, int tau) {
@@ -181,6 +193,26 @@ __device__ __forceinline__ void fwd_rows_body(uint64_t (&x)[1 << LOGE], uint64_t
                                               int tau) {
     constexpr int R = 1 << LOGR, E = 1 << LOGE, T = R / E;
 #define PAD(u) ((u) + ((u) >> LOGE))
+    // The stages after the exchange need E >> (LOGR - st) twiddles per thread
+    // (at least one), read from L2.  When they are few (15 for 256-word rows
+    // of 16 words per thread), all of them are requested here, before the
+    // first stage, so their latency hides behind the stages before the
+    // exchange instead of stalling the ones after it.
+    constexpr int NPRE = PrefetchCount<LOGR, LOGE>::value;
+    ulonglong2 pw[NPRE > 0 ? NPRE : 1];
+    if (NPRE > 0) {
+        int o = 0;
+#pragma unroll
+        for (int st = LOGE; st < LOGR; st++) {
+            const int sh = LOGR - st;
+            const int cnt = sh >= LOGE ? 1 : (E >> sh);
+            const uint32_t base = (1u << (k1 + st)) + (h << st);
+#pragma unroll
+            for (int j = 0; j < cnt; j++)
+                pw[NPRE > 0 ? o + j : 0] = w[base + hi_bits<LOGE>(uint32_t(tau), j << sh, sh)];
+            o += cnt;
+        }
+    }
 #pragma unroll
     for (int st = 0; st < LOGE; st++) {
         const int half = E >> (st + 1);
@@ -196,16 +228,24 @@ __device__ __forceinline__ void fwd_rows_body(uint64_t (&x)[1 << LOGE], uint64_t
     __syncthreads();
 #pragma unroll
     for (int v = 0; v < E; v++) x[v] = s[PAD(tau * E + v)];
+    int o = 0;
 #pragma unroll
     for (int st = LOGE; st < LOGR; st++) {
         const int dist = 1 << (LOGR - 1 - st);
+        const int sh = LOGR - st;
         const uint32_t base = (1u << (k1 + st)) + (h << st);
 #pragma unroll
         for (int v = 0; v < E; v++) {
             if (v & dist) continue;
-            const uint32_t idx = base + hi_bits<LOGE>(uint32_t(tau), v, LOGR - st);
-            fwd_bfly<WIDE>(x[v], x[v + dist], w[idx], q);
+            if (NPRE > 0) {
+                const int j = sh >= LOGE ? 0 : (v >> sh);
+                fwd_bfly<WIDE>(x[v], x[v + dist], pw[NPRE > 0 ? o + j : 0], q);
+            } else {
+                const uint32_t idx = base + hi_bits<LOGE>(uint32_t(tau), v, sh);
+                fwd_bfly<WIDE>(x[v], x[v + dist], w[idx], q);
+            }
         }
+        o += sh >= LOGE ? 1 : (E >> sh);
     }
 #undef PAD
 }
@@ -345,6 +385,24 @@ k_ntt_inv_rows(const uint64_t *src, uint64_t *dst, const LimbMap map,
     uint64_t *s = sm + chl * RP;
 #define PAD(u) ((u) + ((u) >> LOGE))
 
+    // the twiddles of the stages before the exchange (per thread, as in the
+    // forward pass's stages after it) are requested with the data, so that
+    // their latency overlaps the loads and the barrier
+    constexpr int NPRE = PrefetchCount<LOGR, LOGE>::value;
+    ulonglong2 pw[NPRE > 0 ? NPRE : 1];
+    if (NPRE > 0) {
+        int o = 0;
+#pragma unroll
+        for (int st = LOGR - 1; st >= LOGE; st--) {
+            const int sh = LOGR - st;
+            const int cnt = sh >= LOGE ? 1 : (E >> sh);
+            const uint32_t base = (1u << (k1 + st)) + (h << st);
+#pragma unroll
+            for (int j = 0; j < cnt; j++)
+                pw[NPRE > 0 ? o + j : 0] = w[base + hi_bits<LOGE>(uint32_t(tau), j << sh, sh)];
+            o += cnt;
+        }
+    }
     uint64_t x[E];
 #pragma unroll
     for (int v = 0; v < E; v++) s[PAD(tau + T * v)] = ib[tau + T * v];
@@ -352,16 +410,24 @@ k_ntt_inv_rows(const uint64_t *src, uint64_t *dst, const LimbMap map,
 #pragma unroll
     for (int v = 0; v < E; v++) x[v] = s[PAD(tau * E + v)];
     // stages LOGR-1 .. LOGE (distances 1 .. E/2)
+    int o = 0;
 #pragma unroll
     for (int st = LOGR - 1; st >= LOGE; st--) {
         const int dist = 1 << (LOGR - 1 - st);
+        const int sh = LOGR - st;
         const uint32_t base = (1u << (k1 + st)) + (h << st);
 #pragma unroll
         for (int v = 0; v < E; v++) {
             if (v & dist) continue;
-            const uint32_t idx = base + hi_bits<LOGE>(uint32_t(tau), v, LOGR - st);
-            gs_bfly(x[v], x[v + dist], w[idx], q);
+            if (NPRE > 0) {
+                const int j = sh >= LOGE ? 0 : (v >> sh);
+                gs_bfly(x[v], x[v + dist], pw[NPRE > 0 ? o + j : 0], q);
+            } else {
+                const uint32_t idx = base + hi_bits<LOGE>(uint32_t(tau), v, sh);
+                gs_bfly(x[v], x[v + dist], w[idx], q);
+            }
         }
+        o += sh >= LOGE ? 1 : (E >> sh);
     }
 #pragma unroll
     for (int v = 0; v < E; v++) s[PAD(tau * E + v)] = x[v];
@@ -513,7 +579,8 @@ static int run_inv(const Context &c, const uint64_t *src, uint64_t *dst, const L
 // GB300.  Row passes in small CTAs with up to 128 registers per thread
 // measured faster than 80 registers in CTAs of 256 threads, although fewer
 // warps are resident (forward plus inverse of 768 limbs at N = 2^16:
-// 1102 us at 256 threads x 3 CTAs, 1039 at 128 x 4, 1022 at 64 x 8).
+// 1102 us at 256 threads x 3 CTAs, 1039 at 128 x 4, 1022 at 64 x 8, 1018 at
+// 32 x 16; with the later butterflies and twiddle prefetch 946 at 32 x 16).
 #define NTT_SCHEDULES(X)                                                                          \
     X(12, 0, 6, 3, 256, 3, 6, 3, 128, 4) X(12, 1, 6, 3, 256, 3, 6, 3, 256, 3)                    \
     X(12, 2, 5, 3, 256, 3, 7, 4, 128, 4) X(12, 3, 7, 4, 256, 3, 5, 3, 128, 4)                    \
@@ -525,8 +592,8 @@ static int run_inv(const Context &c, const uint64_t *src, uint64_t *dst, const L
     X(15, 0, 7, 4, 256, 3, 8, 4, 64, 8) X(15, 1, 7, 4, 256, 3, 8, 4, 128, 4)                     \
     X(15, 2, 8, 4, 256, 3, 7, 4, 128, 4) X(15, 3, 7, 4, 256, 3, 8, 4, 256, 3)                    \
     X(15, 4, 6, 3, 256, 3, 9, 5, 128, 4)                                                         \
-    X(16, 0, 8, 4, 256, 3, 8, 4, 64, 8) X(16, 1, 8, 4, 256, 3, 8, 4, 128, 4)                     \
-    X(16, 2, 8, 4, 256, 3, 8, 4, 256, 3) X(16, 3, 8, 4, 256, 2, 8, 4, 64, 8)                     \
-    X(16, 4, 8, 4, 256, 3, 8, 4, 32, 16) X(16, 5, 7, 4, 256, 3, 9, 5, 128, 4)
+    X(16, 0, 8, 4, 256, 3, 8, 4, 32, 16) X(16, 1, 8, 4, 256, 3, 8, 4, 64, 8)                     \
+    X(16, 2, 8, 4, 256, 3, 8, 4, 128, 4) X(16, 3, 8, 4, 256, 3, 8, 4, 256, 3)                    \
+    X(16, 4, 8, 4, 256, 2, 8, 4, 64, 8) X(16, 5, 7, 4, 256, 3, 9, 5, 128, 4)
 
 }  // namespace catfhe

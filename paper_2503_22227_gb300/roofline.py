@@ -129,9 +129,9 @@ def bytes_keyswitch(n: int, level: int, L: int, inputs: int, out_level: int, K: 
 # catfhe_measure_int_peak on GB300: the fully reduced Shoup product, the
 # forward butterfly with a conditional subtraction and the wide one.
 SMS = 152
-INSTR_PER_MODMUL = 23.3
-INSTR_PER_BUTTERFLY = 28.5
-INSTR_PER_BUTTERFLY_WIDE = 21.0
+INSTR_PER_MODMUL = 19.1
+INSTR_PER_BUTTERFLY = 23.2
+INSTR_PER_BUTTERFLY_WIDE = 17.2
 
 
 # The integer multiply pipe (ncu: fmaheavy) is the one the arithmetic fills:
@@ -140,7 +140,7 @@ INSTR_PER_BUTTERFLY_WIDE = 21.0
 # those loops).  ncu puts the wide-butterfly loop of catfhe_measure_int_peak
 # at this fraction of the pipe's cycles, so its rate divided by this is the
 # rate of that butterfly with the pipe busy on every cycle.
-LOOP_MUL_PIPE_BUSY = 0.927
+LOOP_MUL_PIPE_BUSY = 0.954
 
 
 def issue_bounds(sm_mhz: float) -> dict:
