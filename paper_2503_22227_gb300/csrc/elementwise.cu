@@ -44,16 +44,16 @@ k_tensor(const TensorArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
     const size_t l0 = size_t(i) * n + x, l1 = (size_t(A.limbs) + i) * n + x;
     const ulonglong2 a0 = ld2(a + l0), a1 = ld2(a + l1), b0 = ld2(b + l0), b1 = ld2(b + l1);
     const size_t o = item * A.out_item + size_t(i) * n + x;
-    // b in Montgomery form (b 2^64 mod q, in [0, 2q), one Shoup product each),
-    // then one Montgomery reduction per output: a b' < 2q^2 and the d1 sum
-    // < 4q^2, both below 2^64 q, so REDC returns a b in [0, 2q)
-    // (measured: batched step 1438.5 -> 1435.2 us against two Shoup products
-    // per 128-bit reduction)
+    // b in Montgomery form (b 2^64 mod q, in [0, 4q), one Shoup product each
+    // on the approximate quotient), then one Montgomery reduction per output:
+    // a b' < 4q^2 and the d1 sum < 8q^2, both below 2^64 q, so REDC returns
+    // a b in [0, 2q) (measured: batched step 1438.5 -> 1435.2 us against two
+    // Shoup products per 128-bit reduction)
     const uint64_t q = m.q;
-    const ulonglong2 c0 = make_ulonglong2(shoup_lazy(b0.x, m.r64, m.r64_s, q),
-                                          shoup_lazy(b0.y, m.r64, m.r64_s, q));
-    const ulonglong2 c1 = make_ulonglong2(shoup_lazy(b1.x, m.r64, m.r64_s, q),
-                                          shoup_lazy(b1.y, m.r64, m.r64_s, q));
+    const ulonglong2 c0 = make_ulonglong2(shoup_lazy4(b0.x, m.r64, m.r64_s, q),
+                                          shoup_lazy4(b0.y, m.r64, m.r64_s, q));
+    const ulonglong2 c1 = make_ulonglong2(shoup_lazy4(b1.x, m.r64, m.r64_s, q),
+                                          shoup_lazy4(b1.y, m.r64, m.r64_s, q));
     U128 p0{0, 0}, p1{0, 0};
     mac(p0, a0.x, c0.x);
     mac(p1, a0.y, c0.y);

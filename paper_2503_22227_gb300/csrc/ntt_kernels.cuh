@@ -351,7 +351,7 @@ k_ntt_fwd_rows(uint64_t *__restrict__ data, const LimbMap map, const DevMod *__r
         for (int v = 0; v < E; v++) {
             const int u = tau + T * v;
             const uint64_t yw = EPI == 2 ? ytile[chl * R + u] : yv[EPI == 1 ? v : 0];
-            uint64_t o = shoup(yw + cq - s[PAD(u)], dv, dvs, q);
+            uint64_t o = csub(csub(shoup_lazy4(yw + cq - s[PAD(u)], dv, dvs, q), 2 * q), q);
             if (ap) o = add_mod(o, ap[u], q);
             op[u] = o;
         }
