@@ -345,49 +345,62 @@ __device__ __forceinline__ uint64_t eval_split(const uint32_t (&al)[KMAX],
 
 // Two adjacent coefficients per thread: every plan constant read from shared
 // memory serves both coefficients' products (one load and one sum of halves
-// instead of two), and sources and results move as 16-byte words.
+// instead of two), and sources and results move as 16-byte words.  The
+// digits' sums of halves are formed once per digit.
+struct Digits2 {
+    template <int K>
+    struct Of {
+        uint32_t l[2][K], h[2][K], s[2][K];
+    };
+};
+
 template <int K>
-__device__ __forceinline__ bool mixed_radix_split_pair(const ulonglong2 (&r)[K], uint32_t (&al)[2][K],
-                                                       uint32_t (&ah)[2][K], bool (&gt)[2],
-                                                       const MontView &P) {
+__device__ __forceinline__ void mixed_radix_split_pair(const ulonglong2 (&r)[K],
+                                                       typename Digits2::template Of<K> &D,
+                                                       bool (&gt)[2], const MontView &P) {
     gt[0] = gt[1] = false;
 #pragma unroll
     for (int j = 0; j < K; j++) {
         Acc3 a0{0, 0, 0}, a1{0, 0, 0};
         const uint64_t wd = ld_plan(&P.C[size_t(j) * K + j]);
-        mac3(a0, uint32_t(r[j].x) & kMask30, uint32_t(r[j].x >> 30), wd);
-        mac3(a1, uint32_t(r[j].y) & kMask30, uint32_t(r[j].y >> 30), wd);
+        const uint32_t dl = uint32_t(wd), dh = uint32_t(wd >> 32), ds = dl + dh;
+        const uint32_t r0l = uint32_t(r[j].x) & kMask30, r0h = uint32_t(r[j].x >> 30);
+        const uint32_t r1l = uint32_t(r[j].y) & kMask30, r1h = uint32_t(r[j].y >> 30);
+        mac3s(a0, r0l, r0h, r0l + r0h, dl, dh, ds);
+        mac3s(a1, r1l, r1h, r1l + r1h, dl, dh, ds);
 #pragma unroll
         for (int i = 0; i < j; i++) {
             const uint64_t w = ld_plan(&P.C[size_t(i) * K + j]);
-            mac3(a0, al[0][i], ah[0][i], w);
-            mac3(a1, al[1][i], ah[1][i], w);
+            const uint32_t wl = uint32_t(w), wh = uint32_t(w >> 32), ws = wl + wh;
+            mac3s(a0, D.l[0][i], D.h[0][i], D.s[0][i], wl, wh, ws);
+            mac3s(a1, D.l[1][i], D.h[1][i], D.s[1][i], wl, wh, ws);
         }
         const uint64_t mj = P.smod[2 * j], mq = P.smod[2 * j + 1];
         const uint64_t a0j = csub(redc(join3(a0), mj, mq), mj);
         const uint64_t a1j = csub(redc(join3(a1), mj, mq), mj);
-        al[0][j] = uint32_t(a0j) & kMask30;
-        ah[0][j] = uint32_t(a0j >> 30);
-        al[1][j] = uint32_t(a1j) & kMask30;
-        ah[1][j] = uint32_t(a1j >> 30);
+        D.l[0][j] = uint32_t(a0j) & kMask30;
+        D.h[0][j] = uint32_t(a0j >> 30);
+        D.s[0][j] = D.l[0][j] + D.h[0][j];
+        D.l[1][j] = uint32_t(a1j) & kMask30;
+        D.h[1][j] = uint32_t(a1j >> 30);
+        D.s[1][j] = D.l[1][j] + D.h[1][j];
         const uint64_t hj = P.h[j];
         if (a0j != hj) gt[0] = a0j > hj;
         if (a1j != hj) gt[1] = a1j > hj;
     }
-    return gt[0] || gt[1];
 }
 
 template <int K>
-__device__ __forceinline__ ulonglong2 eval_split_pair(const uint32_t (&al)[2][K],
-                                                      const uint32_t (&ah)[2][K],
+__device__ __forceinline__ ulonglong2 eval_split_pair(const typename Digits2::template Of<K> &D,
                                                       const bool (&gt)[2], const MontView &P,
                                                       uint32_t t) {
     Acc3 a0{0, 0, 0}, a1{0, 0, 0};
 #pragma unroll
     for (int i = 0; i < K; i++) {
         const uint64_t w = P.Ct[size_t(i) * P.T + t];
-        mac3(a0, al[0][i], ah[0][i], w);
-        mac3(a1, al[1][i], ah[1][i], w);
+        const uint32_t wl = uint32_t(w), wh = uint32_t(w >> 32), ws = wl + wh;
+        mac3s(a0, D.l[0][i], D.h[0][i], D.s[0][i], wl, wh, ws);
+        mac3s(a1, D.l[1][i], D.h[1][i], D.s[1][i], wl, wh, ws);
     }
     const uint64_t mn = P.Mneg[t];
     if (gt[0]) {  // below 2^60 each: ll stays below 2^64
@@ -412,7 +425,7 @@ __device__ __forceinline__ ulonglong2 eval_split_pair(const uint32_t (&al)[2][K]
 // Split-weight layout, every plan of the launch with exactly K sources, two
 // adjacent coefficients per thread (128 threads cover 256 coefficients).
 template <int K>
-__global__ void __launch_bounds__(128, 5)
+__global__ void __launch_bounds__(128, 4)
 k_conv_pair(const PlanList plans, const uint64_t *__restrict__ src, size_t src_item,
             size_t src_plan, uint64_t *__restrict__ dst, size_t dst_item, size_t dst_plan,
             uint32_t log_n) {
@@ -430,12 +443,11 @@ k_conv_pair(const PlanList plans, const uint64_t *__restrict__ src, size_t src_i
     ulonglong2 r[K];
 #pragma unroll
     for (int i = 0; i < K; i++) r[i] = *reinterpret_cast<const ulonglong2 *>(s + P.src_off[i] * n + x);
-    uint32_t al[2][K], ah[2][K];
+    typename Digits2::template Of<K> D;
     bool gt[2];
-    mixed_radix_split_pair<K>(r, al, ah, gt, P);
+    mixed_radix_split_pair<K>(r, D, gt, P);
     for (uint32_t t = 0; t < P.T; t++)
-        *reinterpret_cast<ulonglong2 *>(d + P.dst_off[t] * n + x) =
-            eval_split_pair<K>(al, ah, gt, P, t);
+        *reinterpret_cast<ulonglong2 *>(d + P.dst_off[t] * n + x) = eval_split_pair<K>(D, gt, P, t);
 }
 
 template <int KMAX>

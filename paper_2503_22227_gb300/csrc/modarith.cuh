@@ -179,6 +179,19 @@ __device__ __forceinline__ void mac3(Acc3 &a, uint32_t xl, uint32_t xh, uint64_t
         : "r"(xl), "r"(xh), "r"(wl), "r"(wh));
 }
 
+// mac3 with both sums of halves (xs = xl + xh, ws = wl + wh) computed by the
+// caller, once per digit and once per constant, when each serves several
+// products.
+__device__ __forceinline__ void mac3s(Acc3 &a, uint32_t xl, uint32_t xh, uint32_t xs, uint32_t wl,
+                                      uint32_t wh, uint32_t ws) {
+    asm("{\n\t"
+        "mad.wide.u32 %0, %3, %6, %0;\n\t"
+        "mad.wide.u32 %1, %5, %8, %1;\n\t"
+        "mad.wide.u32 %2, %4, %7, %2;\n\t}"
+        : "+l"(a.ll), "+l"(a.mm), "+l"(a.hh)
+        : "r"(xl), "r"(xh), "r"(xs), "r"(wl), "r"(wh), "r"(ws));
+}
+
 // ll + mm 2^30 + hh 2^60 as 128 bits, mm recovered from kk first.  A term
 // added to ll after the products (the folded -M of the centring) is added to
 // kk too, so that the difference is unchanged.
