@@ -46,6 +46,9 @@ def parse():
                     help="skip the rotation and N=2^14 BFV/BGV side measurements")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the private-query serving sweep")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default NTT schedules (for profiler runs, whose replays "
+                         "would skew the tuner's timings)")
     ap.add_argument("--detail", default=os.path.join(ROOT, "gpurun_out", "bench_detail.json"),
                     help="where the full measurement record (sweeps, schedule tables) goes")
     return ap.parse_args()
@@ -581,8 +584,8 @@ def run_catfhe(args):
     # the NTT schedule of each launch size class this workload uses, picked by
     # the library's tuner (the step's transforms run on 40 to 240 limbs per
     # half batch; the roofline's on 384)
-    tuned = {"<=64": ctx.tune_ntt(2 * L), "<=256": ctx.tune_ntt(4 * L),
-             ">256": ctx.tune_ntt(2 * BATCH * L)}
+    tuned = {} if args.no_tune else {"<=64": ctx.tune_ntt(2 * L), "<=256": ctx.tune_ntt(4 * L),
+                                     ">256": ctx.tune_ntt(2 * BATCH * L)}
 
     def step():
         ctx.mul_relin_rescale(keys, a, b, out)

@@ -420,6 +420,49 @@ __device__ __forceinline__ ulonglong2 eval_split_pair(const typename Digits2::te
     return make_ulonglong2(r0, r1);
 }
 
+// Targets t and t+1 for both coefficients (four independent sums).
+template <int K>
+__device__ __forceinline__ void eval_split_pair2(const typename Digits2::template Of<K> &D,
+                                                 const bool (&gt)[2], const MontView &P,
+                                                 uint32_t t, ulonglong2 &o0, ulonglong2 &o1) {
+    Acc3 a0{0, 0, 0}, a1{0, 0, 0}, b0{0, 0, 0}, b1{0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < K; i++) {
+        const uint64_t w = P.Ct[size_t(i) * P.T + t], v = P.Ct[size_t(i) * P.T + t + 1];
+        const uint32_t wl = uint32_t(w), wh = uint32_t(w >> 32), ws = wl + wh;
+        const uint32_t vl = uint32_t(v), vh = uint32_t(v >> 32), vs = vl + vh;
+        mac3s(a0, D.l[0][i], D.h[0][i], D.s[0][i], wl, wh, ws);
+        mac3s(a1, D.l[1][i], D.h[1][i], D.s[1][i], wl, wh, ws);
+        mac3s(b0, D.l[0][i], D.h[0][i], D.s[0][i], vl, vh, vs);
+        mac3s(b1, D.l[1][i], D.h[1][i], D.s[1][i], vl, vh, vs);
+    }
+    const uint64_t mw = P.Mneg[t], mv = P.Mneg[t + 1];
+    if (gt[0]) {  // below 2^60 each: ll stays below 2^64
+        a0.ll += mw;
+        a0.mm += mw;
+        b0.ll += mv;
+        b0.mm += mv;
+    }
+    if (gt[1]) {
+        a1.ll += mw;
+        a1.mm += mw;
+        b1.ll += mv;
+        b1.mm += mv;
+    }
+    const uint64_t p = P.dmod[2 * t], pi = P.dmod[2 * t + 1];
+    const uint64_t pv = P.dmod[2 * t + 2], piv = P.dmod[2 * t + 3];
+    uint64_t r0 = redc(join3(a0), p, pi), r1 = redc(join3(a1), p, pi);
+    uint64_t s0 = redc(join3(b0), pv, piv), s1 = redc(join3(b1), pv, piv);
+    if (!P.lazy) {
+        r0 = csub(r0, p);
+        r1 = csub(r1, p);
+        s0 = csub(s0, pv);
+        s1 = csub(s1, pv);
+    }
+    o0 = make_ulonglong2(r0, r1);
+    o1 = make_ulonglong2(s0, s1);
+}
+
 // ================================================================== kernels
 
 // Split-weight layout, every plan of the launch with exactly K sources, two
@@ -446,7 +489,14 @@ k_conv_pair(const PlanList plans, const uint64_t *__restrict__ src, size_t src_i
     typename Digits2::template Of<K> D;
     bool gt[2];
     mixed_radix_split_pair<K>(r, D, gt, P);
-    for (uint32_t t = 0; t < P.T; t++)
+    uint32_t t = 0;
+    for (; t + 1 < P.T; t += 2) {
+        ulonglong2 o0, o1;
+        eval_split_pair2<K>(D, gt, P, t, o0, o1);
+        *reinterpret_cast<ulonglong2 *>(d + P.dst_off[t] * n + x) = o0;
+        *reinterpret_cast<ulonglong2 *>(d + P.dst_off[t + 1] * n + x) = o1;
+    }
+    if (t < P.T)
         *reinterpret_cast<ulonglong2 *>(d + P.dst_off[t] * n + x) = eval_split_pair<K>(D, gt, P, t);
 }
 
