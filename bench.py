@@ -126,10 +126,10 @@ class Clocks:
 
 def workload_config(world: int = 1) -> dict:
     """The `config` object of both arms' lines (the same workload)."""
-    return {"workload": "ckks_n16: CKKS N=2^16 L=24 (50-bit q) K=4 (60-bit p) dnum=3, "
-                        "batch of 8 uniform ciphertext pairs, fused HMult+relin+rescale",
+    return {"workload": "ckks_n16: CKKS N=2^16 L=24 (50-bit q) K=4 (60-bit p) dnum=3, batch "
+                        "of 8 uniform pairs, HMult+relin+rescale",
             "N": 1 << 16, "L": 24, "K": 4, "dnum": 3, "batch": BATCH,
-            "l2": "inputs 384 MiB + key 84 MiB per step, larger than L2; no flush",
+            "l2": "inputs 384 MiB + key 84 MiB per step > L2, no flush",
             "parallelism": f"replicas x{world}"}
 
 
@@ -564,6 +564,18 @@ def e2e_leg(ctx, keys, a, b, out, K, world, api, np, torch):
                      "gbs": (h2d + d2h) / tl / 1e9}}
 
 
+def _rounded(x):
+    """The line's floats to 4 significant digits (the full values go to the
+    detail file), so that the one line stays short."""
+    if isinstance(x, float):
+        return float(f"{x:.4g}")
+    if isinstance(x, dict):
+        return {k: _rounded(v) for k, v in x.items()}
+    if isinstance(x, list):
+        return [_rounded(v) for v in x]
+    return x
+
+
 def run_catfhe(args):
     import numpy as np
     import torch
@@ -697,36 +709,43 @@ def run_catfhe(args):
         pv, procs, region, _ = oracle_pool(os.cpu_count() or 1)
         ts = oracle_single_op_seconds()
         cpu = {"value": pv, "unit": UNIT, "cores": procs, "kind": "oracle",
-               "sample": f"{procs} HMult+relin+rescale ops of the workload, one per spawned "
-                         f"process on {procs} cores, {region:.1f}s; one op alone on one "
-                         f"thread {ts:.1f}s ({1.0 / ts:.3f} op/s)"}
+               "sample": f"{procs} ops of the workload, one per process, {region:.1f}s; "
+                         f"1 op on 1 thread {ts:.1f}s"}
     step_ms_sorted = sorted(step_ms)
+    side_short = None
+    if side:
+        side_short = {k: [round(v["value"]), round(v.get("frac", 0), 3)] for k, v in side.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": max(3, args.warmup), "ms_per_step": 1e3 * total_s / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic", "config": workload_config(world),
         "single": {"value": single_value, "batched_over_single": value / world / single_value},
-        "p99_ms": serving["p99_ms"] if serving else None,
         "p50_ms": serving["p50_ms"] if serving else None,
-        "roofline": {"bound": "alu", "kernel": "fwd NTT k_ntt_fwd_cols+k_ntt_fwd_rows, 384 limbs",
-                     "achieved": round(ntt_rate / 1e9, 1), "peak": round(bf_peak / 1e9, 1),
-                     "unit": "Gbutterfly/s", "frac": ntt_rate / bf_peak, "traffic": ntt_traffic(),
-                     "frac_of_issue_bound": ntt_rate / issue["butterfly_wide_per_s"],
+        "p99_ms": serving["p99_ms"] if serving else None,
+        "roofline": {"bound": "alu", "kernel": "fwd NTT, 384 limbs",
+                     "achieved": ntt_rate / 1e9, "peak": bf_peak / 1e9, "unit": "Gbutterfly/s",
+                     "frac": ntt_rate / bf_peak, "traffic": ntt_traffic(),
                      "frac_of_mul_pipe_bound": ntt_rate * R.LOOP_MUL_PIPE_BUSY / bf_peak,
-                     "us": round(ntt_s * 1e6, 1), "hbm_frac": ntt_gbs * 1e9 / hbm},
+                     "frac_of_issue_bound": ntt_rate / issue["butterfly_wide_per_s"],
+                     "us": ntt_s * 1e6},
         "step_roofline": {"frac": t_roof / t_meas, "frac_of_issue_bound": t_roof_issue / t_meas,
-                          "us_per_op": round(t_meas * 1e6, 2),
-                          "roof_us_per_op": round(t_roof * 1e6, 2),
-                          "modmul_peak": mm_peak},
-        "latency_ms": {"p50": step_ms_sorted[len(step_ms) // 2],
-                       "p99": step_ms_sorted[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},
+                          "us_per_op": t_meas * 1e6, "roof_us_per_op": t_roof * 1e6},
         "gpu_launches": int(launches),
-        "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
-        "secondary": side,
-        "serving": ({"saturation_per_s": serving["saturation_per_s"],
-                     "at_offered_per_s": serving["at_offered_per_s"]} if serving else None),
+        "e2e": ({"value": e2e["value"], "unit": UNIT,
+                 "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
+                 "d2h_bytes_per_step": e2e["d2h_bytes_per_step"],
+                 "link_bound_per_s": e2e["link"]["bound_per_s"]} if e2e else None),
+        "cpu_baseline": cpu, "clocks": clk,
+        "secondary": side_short,
+        "saturation_qps": serving["saturation_per_s"] if serving else None,
     }
+    line = _rounded(line)
+    detail["e2e"] = e2e
+    detail["secondary_line"] = side
+    detail["step_latency_ms"] = {"p50": step_ms_sorted[len(step_ms) // 2],
+                                 "p99": step_ms_sorted[min(len(step_ms) - 1,
+                                                           int(0.99 * len(step_ms)))]}
     detail["line"] = line
     detail["ntt_schedules_headline"] = {k: {"chosen": v[0], "us_per_schedule": v[1]}
                                         for k, v in tuned.items()}
