@@ -339,6 +339,28 @@ def secondary(ctx, keys, a, api, W, R, mm_peak, hbm):
         "frac": frac(R.ckks_rotate_hoisted(n, L, K, alpha, len(gs)), hb, th)}
     det["rotations"] = "8 ciphertexts at level 24, r = 1..16 (16 Galois keys); hoisted: one " \
                        "shared ModUp per ciphertext (catfhe_rotate_hoisted)"
+    # device CKKS encode (host slots -> NTT-form plaintext at level 24) and
+    # decode (decrypt + decode -> host slots), one call at a time, wall time
+    # with the host copies of the N/2 slots
+    from paper_2503_22227_gb300 import encoding
+    z = W.complex_slots(W.rng_for("bench-encode"), n)
+    scale = 2.0 ** 50
+    ctx.encode_ckks(z, scale)
+    ct = ctx.encrypt(keys, encoding.encode(z, n, scale), W.seed_for("bench-encode"))
+    ctx.decode_ckks(keys, ct, scale)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(10):
+        ctx.encode_ckks(z, scale)
+    torch.cuda.synchronize()
+    t_enc = (time.perf_counter() - t0) / 10
+    t0 = time.perf_counter()
+    for _ in range(10):
+        ctx.decode_ckks(keys, ct, scale)
+    t_dec = (time.perf_counter() - t0) / 10
+    det["ckks_encode_decode_ms"] = {"encode": t_enc * 1e3, "decode": t_dec * 1e3,
+                                    "note": "N=2^16, level 24, one call at a time, wall time "
+                                            "with the N/2 host slots' copies"}
     for name in ("bfv_n14", "bgv_n14"):
         p = W.PRESETS[name]
         c2 = api.Context(p)
