@@ -58,16 +58,22 @@ k_tensor(const TensorArgs A, const DevMod *__restrict__ mods, uint32_t log_n) {
     mac(p0, a0.x, c0.x);
     mac(p1, a0.y, c0.y);
     st2(A.d0 + o, csub(redc(p0, q, m.qinv), q), csub(redc(p1, q, m.qinv), q));
-    U128 s0{0, 0}, s1{0, 0};
-    mac(s0, a0.x, c1.x);
-    mac(s0, a1.x, c0.x);
-    mac(s1, a0.y, c1.y);
-    mac(s1, a1.y, c0.y);
-    st2(A.d1 + o, csub(redc(s0, q, m.qinv), q), csub(redc(s1, q, m.qinv), q));
     U128 r0{0, 0}, r1{0, 0};
     mac(r0, a1.x, c1.x);
     mac(r1, a1.y, c1.y);
     st2(A.d2 + o, csub(redc(r0, q, m.qinv), q), csub(redc(r1, q, m.qinv), q));
+    // d1 by Karatsuba: (a0 + a1)(b0' + b1') - a0 b0' - a1 b1' = a0 b1' + a1 b0',
+    // one 64 x 64 product instead of two.  a0 + a1 < 2q and b0' + b1' < 8q
+    // each fit one word (q < 2^61), their product (< 16 q^2) fits 128 bits,
+    // and the difference is the same d1 sum as above, below 8 q^2
+    U128 s0{0, 0}, s1{0, 0};
+    mac(s0, a0.x + a1.x, c0.x + c1.x);
+    mac(s1, a0.y + a1.y, c0.y + c1.y);
+    sub128(s0, p0);
+    sub128(s0, r0);
+    sub128(s1, p1);
+    sub128(s1, r1);
+    st2(A.d1 + o, csub(redc(s0, q, m.qinv), q), csub(redc(s1, q, m.qinv), q));
 }
 
 int launch_tensor(const Context &c, const TensorArgs &a, uint32_t count, cudaStream_t s) {

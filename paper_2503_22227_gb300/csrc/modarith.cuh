@@ -130,6 +130,14 @@ __device__ __forceinline__ void mac(U128 &acc, uint64_t a, uint64_t b) {
         : "l"(a), "l"(b));
 }
 
+// a -= b on 128 bits (a >= b).
+__device__ __forceinline__ void sub128(U128 &a, const U128 &b) {
+    asm("sub.cc.u64 %0, %0, %2;\n\t"
+        "subc.u64 %1, %1, %3;"
+        : "+l"(a.lo), "+l"(a.hi)
+        : "l"(b.lo), "l"(b.hi));
+}
+
 // Exact x mod q for any 128-bit x.
 __device__ __forceinline__ uint64_t reduce128(U128 x, const DevMod &m) {
     uint64_t r = shoup_lazy(x.hi, m.r64, m.r64_s, m.q) + shoup_lazy(x.lo, 1, m.one_s, m.q);
