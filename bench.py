@@ -559,7 +559,10 @@ def e2e_leg(ctx, keys, a, b, out, K, world, api, np, torch):
 
     run(3)
     run(3, compute=False)
-    ke = max(3, K // 3)
+    # the same number of steps as the device-resident measurement, so that the
+    # pipeline's fill (first upload) and drain (last compute and download) are
+    # spread over as many steps
+    ke = max(3, K)
     from paper_2503_22227_gb300 import replicas
     barrier(world)
     t0 = time.perf_counter()

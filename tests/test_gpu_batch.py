@@ -45,6 +45,31 @@ def test_every_ntt_schedule_matches_oracle(log_n):
     assert ctx.ntt_schedule(300)[0] == big and ctx.ntt_schedule(24)[0] == chosen
 
 
+def test_every_ntt_schedule_gives_the_same_key_switching():
+    """At N = 2^16 every schedule (row passes of one or several tiles per
+    CTA) must give the same HMult+relin+rescale and HRotate limbs as the
+    default one, which the parity tests tie to the oracle: this runs the
+    unreduced and the combine row passes of each schedule."""
+    p = W.PRESETS["ckks_n16"]
+    ctx = api.Context(p)
+    keys = ctx.keygen(W.seed_for("sched-ks-keys"))
+    g = ctx.galois_elt(3)
+    keys.gen_galois(g)
+    seed = W.seed_for("sched-ks-inputs")
+    level = 6
+    a = torch.cat([ctx.ct_uniform(seed, 2 * i, level) for i in range(4)])
+    b = torch.cat([ctx.ct_uniform(seed, 2 * i + 1, level) for i in range(4)])
+    _, count, _ = ctx.ntt_schedule()
+    ctx.set_ntt_schedule(0)
+    want_m = ctx.mul_relin_rescale(keys, a, b).clone()
+    want_r = ctx.rotate(keys, a, g).clone()
+    for k in range(1, count):
+        ctx.set_ntt_schedule(k)
+        assert torch.equal(ctx.mul_relin_rescale(keys, a, b), want_m), k
+        assert torch.equal(ctx.rotate(keys, a, g), want_r), k
+    ctx.set_ntt_schedule(0)
+
+
 def _ctx(preset, rots):
     ctx = api.Context(preset)
     keys = ctx.keygen(W.seed_for("batch-keys-" + preset.name))
