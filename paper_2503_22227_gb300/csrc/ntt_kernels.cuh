@@ -603,19 +603,28 @@ static int run_inv(const Context &c, const uint64_t *src, uint64_t *dst, const L
 // warps are resident (forward plus inverse of 768 limbs at N = 2^16:
 // 1102 us at 256 threads x 3 CTAs, 1039 at 128 x 4, 1022 at 64 x 8, 1018 at
 // 32 x 16; with the later butterflies and twiddle prefetch 946 at 32 x 16).
+// Column passes of 128 threads at 6 CTAs per SM (as many warps as 256 x 3,
+// in CTAs of half the size, so that each exchange barrier holds 4 warps
+// instead of 8) were faster than 256 x 3 in
+// every size class at N = 2^16: forward plus inverse 481.8 against 484.5 us
+// (largest class), 135.3 against 138.1 (up to 256 limbs), 77.3 against 79.3
+// (up to 64).
 #define NTT_SCHEDULES(X)                                                                          \
     X(12, 0, 6, 3, 256, 3, 6, 3, 128, 4) X(12, 1, 6, 3, 256, 3, 6, 3, 256, 3)                    \
     X(12, 2, 5, 3, 256, 3, 7, 4, 128, 4) X(12, 3, 7, 4, 256, 3, 5, 3, 128, 4)                    \
+    X(12, 4, 6, 3, 128, 6, 6, 3, 128, 4)                                                         \
     X(13, 0, 7, 4, 256, 3, 6, 3, 128, 4) X(13, 1, 7, 4, 256, 3, 6, 3, 64, 8)                     \
     X(13, 2, 7, 4, 256, 3, 6, 3, 256, 3) X(13, 3, 6, 3, 256, 3, 7, 4, 128, 4)                    \
+    X(13, 4, 7, 4, 128, 6, 6, 3, 128, 4)                                                         \
     X(14, 0, 8, 4, 256, 3, 6, 3, 128, 4) X(14, 1, 8, 4, 256, 3, 6, 3, 64, 8)                     \
     X(14, 2, 7, 4, 256, 3, 7, 4, 128, 4) X(14, 3, 8, 4, 256, 3, 6, 3, 256, 3)                    \
-    X(14, 4, 6, 3, 256, 3, 8, 4, 128, 4)                                                         \
+    X(14, 4, 6, 3, 256, 3, 8, 4, 128, 4) X(14, 5, 8, 4, 128, 6, 6, 3, 128, 4)                    \
     X(15, 0, 7, 4, 256, 3, 8, 4, 64, 8) X(15, 1, 7, 4, 256, 3, 8, 4, 128, 4)                     \
     X(15, 2, 8, 4, 256, 3, 7, 4, 128, 4) X(15, 3, 7, 4, 256, 3, 8, 4, 256, 3)                    \
-    X(15, 4, 6, 3, 256, 3, 9, 5, 128, 4)                                                         \
-    X(16, 0, 8, 4, 256, 3, 8, 4, 32, 16) X(16, 1, 8, 4, 256, 3, 8, 4, 64, 8)                     \
+    X(15, 4, 6, 3, 256, 3, 9, 5, 128, 4) X(15, 5, 7, 4, 128, 6, 8, 4, 64, 8)                     \
+    X(16, 0, 8, 4, 128, 6, 8, 4, 32, 16) X(16, 1, 8, 4, 256, 3, 8, 4, 64, 8)                     \
     X(16, 2, 8, 4, 256, 3, 8, 4, 128, 4) X(16, 3, 8, 4, 256, 3, 8, 4, 256, 3)                    \
-    X(16, 4, 8, 4, 256, 2, 8, 4, 64, 8) X(16, 5, 7, 4, 256, 3, 9, 5, 128, 4)
+    X(16, 4, 8, 4, 256, 2, 8, 4, 64, 8) X(16, 5, 7, 4, 256, 3, 9, 5, 128, 4)                     \
+    X(16, 6, 8, 4, 256, 3, 8, 4, 32, 16) X(16, 7, 8, 4, 128, 5, 8, 4, 32, 16)
 
 }  // namespace catfhe
