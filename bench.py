@@ -283,7 +283,7 @@ def uneven_mix(api, W, R, mm_peak, n_ops=256, lanes=8, reps=5):
         ops.append(api.make_op(kind, c, a, out, keys=k, b=b, galois_elt=g))
         keep.append((a, b, out))
         if kind == api.OP_MUL_RELIN:
-            w = R.ckks_mul_relin_rescale(c.n, level, c.K, c.alpha).modmuls
+            w = R.ckks_mul_relin(c.n, level, c.K, c.alpha).modmuls
         elif kind == api.OP_ROTATE:
             w = R.ckks_rotate(c.n, level, c.K, c.alpha).modmuls
         else:

@@ -60,6 +60,13 @@ def ckks_mul_relin_rescale(n: int, level: int, K: int, alpha: int) -> Work:
     return Work(ntt, prod, n)
 
 
+def ckks_mul_relin(n: int, level: int, K: int, alpha: int) -> Work:
+    """CKKS HMult + relinearise without the rescale: the tensor, then the same
+    key switching as a rotation (ModDown divides by P alone)."""
+    w = ckks_rotate(n, level, K, alpha)
+    return Work(w.limb_ntts, w.coeff_products + 4 * level, n)
+
+
 def ckks_rotate(n: int, level: int, K: int, alpha: int) -> Work:
     M = level + K
     ds = digits(level, alpha)

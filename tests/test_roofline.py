@@ -46,6 +46,17 @@ def test_secondary_counts():
     assert abs(h.coeff_products - (416 + 504 / 16)) < 1e-9
 
 
+def test_mul_relin_without_rescale_counts():
+    """HMult + relinearise alone at N = 2^16, L = 24, K = 4, alpha = 8: INTT of
+    d2 (24), 3 digits x 20 lifted limbs (60), INTT of the 4 P limbs of both
+    polynomials (8), NTT of their lift to the 24 q limbs (48); products: the
+    tensor (96), ModUp 3 x (8 + 8 x 20) = 504, the key inner product
+    2 x 3 x 28 = 168, ModDown 2 x (4 + 4 x 24) = 200 and the final 2 x 24."""
+    w = R.ckks_mul_relin(1 << 16, 24, 4, 8)
+    assert w.limb_ntts == 24 + 60 + 8 + 48
+    assert w.coeff_products == 96 + 504 + 168 + 200 + 48
+
+
 def test_keyswitch_bytes_and_issue_bounds():
     n = 1 << 16
     # a rotation reads one ciphertext, writes one, and shares the key over 8
