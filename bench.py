@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default NTT schedules (for profiler runs, whose replays "
                          "would skew the tuner's timings)")
-    ap.add_argument("--detail", default=os.path.join(ROOT, "gpurun_out", "bench_detail.json"),
+    ap.add_argument("--detail", default=os.path.join(ROOT, "bench_out", "bench_detail.json"),
                     help="where the full measurement record (sweeps, schedule tables) goes")
     return ap.parse_args()
 
