@@ -462,7 +462,8 @@ void catfhe_graph_destroy(catfhe_graph *graph);
 
 /* ---- NTT schedules (paper Sec. 3.1.3) ----
  * Each ring degree has a few two-pass schedules (how many of the log N
- * stages the column pass takes, and how many words each thread holds).  The
+ * stages the column pass takes, how many words each thread holds, and each
+ * pass's threads per CTA and CTAs per SM).  The
  * context keeps one choice per launch size class: launches of up to 64
  * limbs, up to 256, and more.  catfhe_tune_ntt times every schedule of
  * ctx's ring degree on `limbs` limbs (rounded up to whole groups of L;
