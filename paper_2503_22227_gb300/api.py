@@ -577,15 +577,24 @@ def make_op(kind: int, ctx: "Context", a, out, keys: "Keys" = None, b=None, galo
     [count][2][level][N] of ctx's ring degree (for MUL_PLAIN `b` is a
     plaintext from plain_import).  galois_elt for rotations, const (int64)
     for MUL_INT / ADD_CONST; DROP takes the level of `out`."""
+    count, _, level, _ = a.shape
+    return make_op_ptr(kind, ctx, count, level, out.shape[2], a.data_ptr(),
+                       b.data_ptr() if b is not None else None, out.data_ptr(), keys=keys,
+                       galois_elt=galois_elt, const=const)
+
+
+def make_op_ptr(kind: int, ctx: "Context", count: int, level: int, level_out: int, a: int,
+                b, out: int, keys: "Keys" = None, galois_elt: int = 0, const: int = 0) -> Op:
+    """make_op from device addresses: `a` (and `b`, or None) hold
+    [count][2][level][N] words, `out` [count][2][level_out][N]."""
     o = Op()
     o.op = kind
-    o.count, _, o.level, _ = a.shape
-    o.level_out = out.shape[2]
+    o.count, o.level, o.level_out = count, level, level_out
     o.ctx = ctx._h.value
     o.keys = keys._h.value if keys is not None else None
-    o.a = a.data_ptr()
-    o.b = b.data_ptr() if b is not None else None
-    o.out = out.data_ptr()
+    o.a = a
+    o.b = b
+    o.out = out
     o.arg = galois_elt if kind == OP_ROTATE else (const & 0xFFFFFFFFFFFFFFFF)
     return o
 

@@ -310,11 +310,63 @@ def schedule(circuit: Circuit) -> Schedule:
     return sch
 
 
+@dataclass
+class MemoryPlan:
+    """Byte offsets of a circuit's intermediate ciphertexts in one arena per
+    request.  A node's buffer is live from its stage to the last stage that
+    reads it (outputs: to the end); two nodes share bytes only if one's last
+    reader runs in an earlier stage than the other's own stage, so that no
+    batch (one stage of many requests) reads memory that it also writes."""
+    offsets: dict
+    sizes: dict
+    live: dict          # node id -> (first stage, last stage)
+    size: int
+
+
+def memory_plan(circuit: Circuit, align: int = 256) -> MemoryPlan:
+    """First fit, stage by stage, against the buffers live in that stage."""
+    cached = getattr(circuit, "_memory_plan", None)
+    if cached is not None and cached[0] == len(circuit.nodes):
+        return cached[1]
+    alive = circuit.live()
+    last = {}
+    for nd in circuit.nodes:
+        if nd.id in alive:
+            for a in nd.args:
+                last[a] = max(last.get(a, 0), nd.stage)
+    end = 1 << 30
+    for o in circuit.outputs.values():
+        last[o] = end
+    offsets, sizes, live = {}, {}, {}
+    for st in circuit.stages():
+        s = circuit.nodes[st[0]].stage
+        busy = sorted((offsets[i], offsets[i] + sizes[i]) for i in offsets if live[i][1] >= s)
+        for i in st:
+            size = 2 * circuit.nodes[i].level * circuit.n * 8
+            off = 0
+            for a, b in busy:
+                if a >= off + size:
+                    break
+                if b > off:
+                    off = (b + align - 1) // align * align
+            offsets[i], sizes[i], live[i] = off, size, (s, last.get(i, s))
+            busy = sorted(busy + [(off, off + size)])
+    total = max((offsets[i] + sizes[i] for i in offsets), default=0)
+    plan = MemoryPlan(offsets, sizes, live, total)
+    circuit._memory_plan = (len(circuit.nodes), plan)
+    return plan
+
+
 class Runner:
     """One request's instance of a circuit: device buffers per node, the
-    batch entries of the current stage, and buffer release after last use."""
+    batch entries of the current stage, and buffer release after last use.
 
-    def __init__(self, circuit: Circuit, ctx, keys, inputs: dict):
+    With `arena` (a device byte tensor of memory_plan(circuit).size bytes)
+    every intermediate lives at its planned offset there, and the entries of
+    every stage are built once, here: a tick then only gathers them, with no
+    allocation or entry marshalling per operation."""
+
+    def __init__(self, circuit: Circuit, ctx, keys, inputs: dict, arena=None):
         self.c = circuit
         self.ctx, self.keys = ctx, keys
         self.buf: dict[int, object] = {}
@@ -322,6 +374,25 @@ class Runner:
             self.buf[i] = inputs[name]
         self.sch = schedule(circuit)
         self.pos = 0
+        self.arena = arena
+        self.ops = None
+        if arena is not None:
+            plan = memory_plan(circuit)
+            base = arena.data_ptr()
+            ptr = {i: base + off for i, off in plan.offsets.items()}
+            for i, t in self.buf.items():
+                ptr[i] = t.data_ptr()
+            nodes = circuit.nodes
+            self.ops = []
+            for entries in self.sch.stages:
+                ops = []
+                for i, kind, args, level, arg in entries:
+                    ops.append(api.make_op_ptr(
+                        kind, ctx, 1, nodes[args[0]].level, level, ptr[args[0]],
+                        ptr[args[1]] if len(args) > 1 else None, ptr[i], keys=keys,
+                        galois_elt=arg if kind == api.OP_ROTATE else 0,
+                        const=0 if kind == api.OP_ROTATE else arg))
+                self.ops.append(ops)
 
     @property
     def done(self) -> bool:
@@ -332,6 +403,8 @@ class Runner:
         return len(self.sch.stages) - self.pos
 
     def stage_ops(self) -> list:
+        if self.ops is not None:
+            return self.ops[self.pos]
         ops = []
         for i, kind, args, level, arg in self.sch.stages[self.pos]:
             a = self.buf[args[0]]
@@ -346,15 +419,24 @@ class Runner:
     def advance(self) -> None:
         """Drops the buffers last read by the current stage; call it only
         after that stage has been enqueued."""
-        for i in self.sch.release[self.pos]:
-            self.buf.pop(i, None)
+        if self.ops is None:
+            for i in self.sch.release[self.pos]:
+                self.buf.pop(i, None)
         self.pos += 1
 
     def result(self, name: str):
-        return self.buf[self.c.outputs[name]]
+        i = self.c.outputs[name]
+        if self.ops is None:
+            return self.buf[i]
+        plan = memory_plan(self.c)
+        import torch
+        words = self.arena.narrow(0, plan.offsets[i], plan.sizes[i]).view(torch.int64)
+        return words.view(1, 2, self.c.nodes[i].level, self.c.n)
 
     def release(self) -> None:
         self.buf.clear()
+        self.arena = None
+        self.ops = None
 
 
 def pdq_circuit(ctx, delta: float, coeffs, kappa: float = 1.0, sum_slots: int = 1024,

@@ -255,7 +255,10 @@ class Table:
             self.uploads.append(pair)
         torch.cuda.synchronize()
         self.ct_bytes = 2 * ctx.L * ctx.n * 8
-        self.need = self.circuit.peak_bytes() + 2 * self.ct_bytes
+        # one arena per request for the circuit's intermediates, plus the two
+        # uploaded bounds
+        self.arena_bytes = circuit.memory_plan(self.circuit).size
+        self.need = self.arena_bytes + 2 * self.ct_bytes
 
     def avg_circuit(self):
         if getattr(self, "_avg_circuit", None) is None:
@@ -300,7 +303,11 @@ class GpuEngine:
     """Runs requests' circuit stages as uneven batches over `lanes` streams.
     Uploads and result copies are asynchronous (page-locked host buffers,
     stream-ordered), so no tick waits for the host; result buffers come from
-    a pool and return to it when the request retires."""
+    a pool and return to it when the request retires.  Each request's
+    intermediates live in one device arena laid out by the circuit's memory
+    plan, and its batch entries are built once when it starts (a tick
+    concatenates them), so the host does no allocation and no marshalling
+    per operation."""
 
     def __init__(self, table: Table, lanes: int = 8, keep_results: bool = True,
                  profile: bool = False):
@@ -335,9 +342,11 @@ class GpuEngine:
         lo_h, hi_h = self.t.uploads[req.bounds]
         lo = ctx.import_ct(lo_h, api.FORM_NATIVE | api.FORM_ASYNC)
         hi = ctx.import_ct(hi_h, api.FORM_NATIVE | api.FORM_ASYNC)
+        arena = self.torch.empty(self.t.arena_bytes, dtype=self.torch.uint8, device="cuda")
         req.state = self.circuit_mod.Runner(self.t.circuit, ctx, self.t.keys,
                                             {"x": self.t.columns[req.col_a],
-                                             "y": self.t.columns[req.col_b], "lo": lo, "hi": hi})
+                                             "y": self.t.columns[req.col_b], "lo": lo, "hi": hi},
+                                            arena=arena)
 
     def stage(self, reqs) -> list:
         t0 = time.perf_counter()

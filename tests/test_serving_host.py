@@ -260,37 +260,60 @@ def test_idle_gaps_do_not_count_as_latency():
 
 
 # ----------------------------------------------------------------------------
-# The GPU engine's buffer lifetimes, with a fake allocator that recycles
-# addresses as soon as a buffer is dropped (as a caching allocator may).
+# The GPU engine's memory, with a fake allocator of real sizes that recycles
+# an address as soon as its buffer is dropped (as a caching allocator may).
 
 class _Alloc:
     def __init__(self):
-        self.free, self.next, self.live = [], 1 << 20, set()
+        self.free, self.next, self.live = {}, 1 << 20, {}
 
-    def take(self):
-        addr = self.free.pop() if self.free else self.next
-        if addr == self.next:
-            self.next += 1 << 20
-        self.live.add(addr)
+    def take(self, size):
+        spare = self.free.get(size)
+        if spare:
+            addr = spare.pop()
+        else:
+            addr = self.next
+            self.next += (size + 4095) // 4096 * 4096
+        self.live[addr] = size
         return addr
 
     def give(self, addr):
-        self.live.discard(addr)
-        self.free.append(addr)
+        size = self.live.pop(addr)
+        self.free.setdefault(size, []).append(addr)
+
+    def holds(self, lo, hi):
+        import bisect
+        bases = sorted(self.live)
+        k = bisect.bisect_right(bases, lo) - 1
+        return k >= 0 and hi <= bases[k] + self.live[bases[k]]
 
 
 class _Buf:
-    def __init__(self, alloc, shape):
+    def __init__(self, alloc, shape=None, nbytes=None):
         import weakref
         self.shape = shape
-        self._p = alloc.take()
+        self.nbytes = nbytes if nbytes is not None else 8 * int(np.prod(shape))
+        self._p = alloc.take(self.nbytes)
         weakref.finalize(self, alloc.give, self._p)
 
     def data_ptr(self):
         return self._p
 
+    def numel(self):
+        return self.nbytes
+
+    # the views a runner takes of its arena for its results
+    def narrow(self, dim, start, length):
+        return self
+
+    def view(self, *shape):
+        if shape and all(isinstance(d, int) for d in shape):
+            return types.SimpleNamespace(shape=shape, data_ptr=self.data_ptr)
+        return self
+
 
 def _fake_table(alloc, batches):
+    import bisect
     import ctypes
     from paper_2503_22227_gb300 import api as real_api
 
@@ -301,12 +324,21 @@ def _fake_table(alloc, batches):
     ctx.export_into = lambda ct, host, form: host
     keys = types.SimpleNamespace(_h=ctypes.c_void_p(2))
 
+    def span(ptr, count, level):
+        return ptr, ptr + count * 2 * level * ctx.n * 8
+
     def run_batch(entries, lanes, ws):
-        ins = {e.a for e in entries} | {e.b for e in entries if e.b}
-        outs = [e.out for e in entries]
-        assert len(set(outs)) == len(outs), "two outputs share memory"
-        assert not (ins & set(outs)), "an output overwrites an input of the same batch"
-        assert ins <= alloc.live and set(outs) <= alloc.live, "a batch reads released memory"
+        outs = sorted(span(e.out, e.count, e.level_out) for e in entries)
+        ins = [span(e.a, e.count, e.level) for e in entries]
+        ins += [span(e.b, e.count, e.level) for e in entries if e.b]
+        for (a0, a1), (b0, b1) in zip(outs, outs[1:]):
+            assert a1 <= b0, "two outputs of one batch share memory"
+        starts = [o[0] for o in outs]
+        for lo, hi in ins:
+            k = bisect.bisect_left(starts, hi) - 1
+            assert k < 0 or outs[k][1] <= lo, "an output overwrites an input of the same batch"
+        for lo, hi in ins + outs:
+            assert alloc.holds(lo, hi), "a batch touches memory that is not allocated"
         batches.append(len(entries))
 
     class _Batch:
@@ -336,24 +368,47 @@ def _fake_table(alloc, batches):
         def clone(self):
             return self
 
-    class _Ws:
-        def numel(self):
-            return 1 << 30
+    def empty(*a, **k):
+        if k.get("pin_memory"):
+            return _Host()
+        return _Buf(alloc, nbytes=int(a[0]))
 
-    fake_torch = types.SimpleNamespace(
-        uint8=None, int64=None,
-        empty=lambda *a, **k: _Host() if k.get("pin_memory") else _Ws(),
-        cuda=types.SimpleNamespace(Event=_Event))
+    fake_torch = types.SimpleNamespace(uint8=None, int64=None, empty=empty,
+                                       cuda=types.SimpleNamespace(Event=_Event))
     t = S.Table.__new__(S.Table)
     t.api, t.torch, t.ctx, t.keys = fake_api, fake_torch, ctx, keys
     t.circuit = C.pdq_circuit(ctx, 2.0 ** 50, S.sign_coefficients())
     t.columns = [_Buf(alloc, (1, 2, ctx.L, ctx.n)) for _ in range(S.COLS)]
     t.uploads = [(None, None)] * 4
-    t.need = t.circuit.peak_bytes()
+    t.arena_bytes = C.memory_plan(t.circuit).size
+    t.ct_bytes = 2 * ctx.L * ctx.n * 8
+    t.need = t.arena_bytes + 2 * t.ct_bytes
     return t
 
 
-def test_gpu_engine_never_recycles_a_buffer_inside_its_batch():
+def test_memory_plan_keeps_every_stage_disjoint():
+    """In every stage the buffers live then (written in it, read in it or
+    later) occupy disjoint bytes of the arena, within its size, which is at
+    least the circuit's peak of live bytes and not far above it."""
+    c = C.pdq_circuit(_ctx(), 2.0 ** 50, S.sign_coefficients())
+    plan = C.memory_plan(c)
+    assert set(plan.offsets) == {i for st in c.stages() for i in st}
+    for st in c.stages():
+        s = c.nodes[st[0]].stage
+        spans = sorted((plan.offsets[i], plan.offsets[i] + plan.sizes[i])
+                       for i in plan.offsets if plan.live[i][0] <= s <= plan.live[i][1])
+        for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
+            assert a1 <= b0, s
+        assert spans[-1][1] <= plan.size
+        # every argument read in this stage is live in it
+        for i in st:
+            for a in c.nodes[i].args:
+                if a in plan.live:
+                    assert plan.live[a][0] < s <= plan.live[a][1]
+    assert c.peak_bytes() <= plan.size <= 1.1 * c.peak_bytes()
+
+
+def test_gpu_engine_batches_touch_only_their_own_live_memory():
     alloc, batches = _Alloc(), []
     table = _fake_table(alloc, batches)
     eng = S.GpuEngine(table, lanes=4)
@@ -365,5 +420,5 @@ def test_gpu_engine_never_recycles_a_buffer_inside_its_batch():
     assert st.served == 12 and max(batches) > 45
     assert all(r.result is not None for r in reqs)
     del reqs, eng
-    # every intermediate went back: only the table columns stay allocated
+    # every request's arena and uploads went back: only the table columns stay
     assert len(alloc.live) == S.COLS
