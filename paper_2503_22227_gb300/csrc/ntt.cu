@@ -35,9 +35,9 @@ NTT_DECL(12) NTT_DECL(13) NTT_DECL(14) NTT_DECL(15) NTT_DECL(16)
 
 int ntt_schedule_count(int log_n) {
     switch (log_n) {
-        case 12: case 13: return 5;
-        case 14: case 15: return 6;
-        case 16: return 8;
+        case 12: return 5;
+        case 13: return 7;
+        case 14: case 15: case 16: return 8;
         default: return 0;
     }
 }

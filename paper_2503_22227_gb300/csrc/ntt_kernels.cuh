@@ -608,20 +608,27 @@ static int run_inv(const Context &c, const uint64_t *src, uint64_t *dst, const L
 // instead of 8) were faster than 256 x 3 in
 // every size class at N = 2^16: forward plus inverse 481.8 against 484.5 us
 // (largest class), 135.3 against 138.1 (up to 256 limbs), 77.3 against 79.3
-// (up to 64).
-#define NTT_SCHEDULES(X)                                                                          \
+// (up to 64).  At 2^13 - 2^15 the same column pass with row passes of 32
+// threads x 16 CTAs per SM (up to 128 registers) was the fastest for the
+// largest class: forward plus inverse 111.2 against 116.1 us (2^13, 16
+// ciphertexts of 24 primes), 228.2 against 237.1 (2^14), 452.5 against
+// 464.4 (2^15).
+#define NTT_SCHEDULES(X)                                                                         \
     X(12, 0, 6, 3, 256, 3, 6, 3, 128, 4) X(12, 1, 6, 3, 256, 3, 6, 3, 256, 3)                    \
     X(12, 2, 5, 3, 256, 3, 7, 4, 128, 4) X(12, 3, 7, 4, 256, 3, 5, 3, 128, 4)                    \
     X(12, 4, 6, 3, 128, 6, 6, 3, 128, 4)                                                         \
-    X(13, 0, 7, 4, 256, 3, 6, 3, 128, 4) X(13, 1, 7, 4, 256, 3, 6, 3, 64, 8)                     \
+    X(13, 0, 7, 4, 128, 6, 6, 3, 32, 16) X(13, 1, 7, 4, 256, 3, 6, 3, 64, 8)                     \
     X(13, 2, 7, 4, 256, 3, 6, 3, 256, 3) X(13, 3, 6, 3, 256, 3, 7, 4, 128, 4)                    \
-    X(13, 4, 7, 4, 128, 6, 6, 3, 128, 4)                                                         \
-    X(14, 0, 8, 4, 256, 3, 6, 3, 128, 4) X(14, 1, 8, 4, 256, 3, 6, 3, 64, 8)                     \
+    X(13, 4, 7, 4, 128, 6, 6, 3, 128, 4) X(13, 5, 7, 4, 256, 3, 6, 3, 128, 4)                    \
+    X(13, 6, 7, 4, 128, 6, 6, 3, 64, 8)                                                          \
+    X(14, 0, 8, 4, 128, 6, 6, 3, 32, 16) X(14, 1, 8, 4, 256, 3, 6, 3, 64, 8)                     \
     X(14, 2, 7, 4, 256, 3, 7, 4, 128, 4) X(14, 3, 8, 4, 256, 3, 6, 3, 256, 3)                    \
     X(14, 4, 6, 3, 256, 3, 8, 4, 128, 4) X(14, 5, 8, 4, 128, 6, 6, 3, 128, 4)                    \
-    X(15, 0, 7, 4, 256, 3, 8, 4, 64, 8) X(15, 1, 7, 4, 256, 3, 8, 4, 128, 4)                     \
+    X(14, 6, 8, 4, 256, 3, 6, 3, 128, 4) X(14, 7, 8, 4, 128, 6, 6, 3, 64, 8)                     \
+    X(15, 0, 7, 4, 128, 6, 8, 4, 32, 16) X(15, 1, 7, 4, 256, 3, 8, 4, 128, 4)                    \
     X(15, 2, 8, 4, 256, 3, 7, 4, 128, 4) X(15, 3, 7, 4, 256, 3, 8, 4, 256, 3)                    \
     X(15, 4, 6, 3, 256, 3, 9, 5, 128, 4) X(15, 5, 7, 4, 128, 6, 8, 4, 64, 8)                     \
+    X(15, 6, 7, 4, 256, 3, 8, 4, 64, 8) X(15, 7, 7, 4, 128, 6, 8, 4, 128, 4)                     \
     X(16, 0, 8, 4, 128, 6, 8, 4, 32, 16) X(16, 1, 8, 4, 256, 3, 8, 4, 64, 8)                     \
     X(16, 2, 8, 4, 256, 3, 8, 4, 128, 4) X(16, 3, 8, 4, 256, 3, 8, 4, 256, 3)                    \
     X(16, 4, 8, 4, 256, 2, 8, 4, 64, 8) X(16, 5, 7, 4, 256, 3, 9, 5, 128, 4)                     \
