@@ -369,7 +369,9 @@ def secondary(ctx, keys, a, api, W, R, mm_peak, hbm):
         x = torch.cat([c2.ct_uniform(seed, 2 * i, p.L) for i in range(p.batch)])
         y = torch.cat([c2.ct_uniform(seed, 2 * i + 1, p.L) for i in range(p.batch)])
         o = c2.empty_ct(p.batch, p.L)
+        torch.cuda.nvtx.range_push(name)  # a profiler's filter for this configuration
         t = _time(lambda: c2.mul_relin(k2, x, y, o), 10) / p.batch
+        torch.cuda.nvtx.range_pop()
         if p.scheme == W.BFV:
             w = R.bfv_mul_relin(c2.n, p.L, c2.K, c2.alpha, c2.nb)
         else:

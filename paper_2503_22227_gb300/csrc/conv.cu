@@ -30,6 +30,7 @@
 // One thread handles one coefficient of one item; the packed plan (a few
 // KB) sits in shared memory and every thread reads the same words
 // (broadcast).
+#include <cmath>
 #include "launch.cuh"
 #include "modarith.cuh"
 
@@ -685,6 +686,35 @@ int launch_conv(const Context &c, const PlanList &plans, const uint64_t *src, si
     return cudaGetLastError() == cudaSuccess ? CATFHE_OK : CATFHE_ECUDA;
 }
 
+// Coefficients per thread of a grid-stride launch over `items` rows of n
+// coefficients, 256 threads per CTA: the count (1 to 8) whose last wave of
+// CTAs is the fullest, given the resident CTAs per SM of `kernel` (more per
+// thread on a tie, which spreads each CTA's plan copy over more work).  At
+// N = 2^14, 24 rows and 2 CTAs per SM on 152 SMs, 4 per thread (the fixed
+// choice before) leaves the second of two waves three-quarters empty.
+template <typename K>
+static unsigned stride_columns(K kernel, size_t smem, size_t n, uint32_t items) {
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 256, smem) != cudaSuccess ||
+        sms <= 0 || occ <= 0)
+        return unsigned((n + 1023) / 1024);
+    const double slots = double(sms) * occ;
+    double best = -1.0;
+    unsigned cols = unsigned((n + 1023) / 1024);
+    for (unsigned per = 1; per <= 8; per++) {
+        const unsigned x = unsigned((n + 256 * per - 1) / (256 * per));
+        const double waves = double(x) * items / slots;
+        const double fill = waves / std::ceil(waves);
+        if (fill >= best - 1e-9) {
+            best = fill;
+            cols = x;
+        }
+    }
+    return cols;
+}
+
 int launch_bfv_scale_round(const Context &c, const uint64_t *q_to_b, uint32_t q_to_b_words,
                            const uint64_t *b_to_q, uint32_t b_to_q_words, const uint64_t *src,
                            size_t src_item, uint64_t *dst, size_t dst_item, uint32_t items,
@@ -693,16 +723,18 @@ int launch_bfv_scale_round(const Context &c, const uint64_t *q_to_b, uint32_t q_
     const uint64_t *tq = q_to_b + q_to_b_words;
     const size_t n = c.n;
     const uint32_t kq = uint32_t(c.L), kb = uint32_t(c.nb);
-    dim3 grid(unsigned((n + 1023) / 1024), items, 1);
     const size_t sm = size_t(q_to_b_words + b_to_q_words + 2 * kb) * 8;
     if (kq <= 8 && kb <= 8) {
+        const dim3 grid(stride_columns(k_bfv_scale_round<8, 8>, sm, n, items), items, 1);
         k_bfv_scale_round<8, 8><<<grid, 256, sm, s>>>(q_to_b, b_to_q, tq, q_to_b_words, b_to_q_words,
                                                      src, src_item, dst, dst_item, c.log_n);
     } else if (kq <= 16 && kb <= 16) {
+        const dim3 grid(stride_columns(k_bfv_scale_round<16, 16>, sm, n, items), items, 1);
         k_bfv_scale_round<16, 16><<<grid, 256, sm, s>>>(q_to_b, b_to_q, tq, q_to_b_words,
                                                         b_to_q_words, src, src_item, dst, dst_item,
                                                         c.log_n);
     } else {
+        const dim3 grid(stride_columns(k_bfv_scale_round<32, 32>, sm, n, items), items, 1);
         k_bfv_scale_round<32, 32><<<grid, 256, sm, s>>>(q_to_b, b_to_q, tq, q_to_b_words,
                                                         b_to_q_words, src, src_item, dst, dst_item,
                                                         c.log_n);
