@@ -690,8 +690,8 @@ int launch_conv(const Context &c, const PlanList &plans, const uint64_t *src, si
 // coefficients, 256 threads per CTA: the count (1 to 8) whose last wave of
 // CTAs is the fullest, given the resident CTAs per SM of `kernel` (more per
 // thread on a tie, which spreads each CTA's plan copy over more work).  At
-// N = 2^14, 24 rows and 2 CTAs per SM on 152 SMs, 4 per thread (the fixed
-// choice before) leaves the second of two waves three-quarters empty.
+// N = 2^14 with 24 rows and 4 resident CTAs per SM on 152 SMs, 4 per thread
+// (the fixed choice before) fills 63% of one wave; 3 per thread fills 87%.
 template <typename K>
 static unsigned stride_columns(K kernel, size_t smem, size_t n, uint32_t items) {
     int dev = 0, sms = 0, occ = 0;
