@@ -6,6 +6,7 @@
 // All are HBM-bound streams over limb-major data: one thread per coefficient,
 // consecutive threads on consecutive words, grids sized by the data (a whole
 // batch of ciphertexts per launch).
+#include <cmath>
 #include "bulk.cuh"
 #include "launch.cuh"
 #include "modarith.cuh"
@@ -207,10 +208,17 @@ struct IpTile {
     static constexpr uint32_t value = BETA <= 4 ? 512 : 256;
 };
 
+// blockIdx.z: a group of consecutive ciphertexts of the launch (the host
+// splits them when one group per tile would leave the last wave of CTAs
+// mostly empty); each group's CTA loads its key tiles once.
 template <int BETA>
 __global__ void __launch_bounds__(IpTile<BETA>::value / 2)
 k_ip_bulk(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n, uint32_t count) {
     grid_dep_wait();
+    const uint32_t per = (count + gridDim.z - 1) / gridDim.z;
+    const uint32_t first = blockIdx.z * per;
+    if (first >= count) return;  // an empty group (the whole CTA, before any barrier)
+    const uint32_t nloc = count - first < per ? count - first : per;
     constexpr uint32_t kIpTile = IpTile<BETA>::value;
     extern __shared__ __align__(128) uint64_t sm[];
     __shared__ __align__(8) uint64_t bars[3];  // buffer 0, buffer 1, keys
@@ -227,7 +235,8 @@ k_ip_bulk(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n, uint3
     uint64_t *sbuf[2] = {sm + 2 * BETA * kIpTile, sm + (3 * BETA + 2) * kIpTile};
     const uint32_t item_bytes = (beta + (f0 ? 1 : 0) + (f1 ? 1 : 0)) * TB;
 
-    auto issue_item = [&](uint32_t item, uint32_t b) {
+    auto issue_item = [&](uint32_t k, uint32_t b) {  // the group's k-th ciphertext
+        const uint32_t item = first + k;
         uint64_t *dst = sbuf[b];
         mbar_expect_tx(&bars[b], item_bytes);
         const uint64_t *ext = A.ext + item * A.ext_item;
@@ -254,15 +263,15 @@ k_ip_bulk(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n, uint3
             bulk_load(skey + (2 * j + 1) * kIpTile, A.key + ((size_t(j) * 2 + 1) * KL + A.key_limb[i]) * n + x0, TB, &bars[2]);
         }
         issue_item(0, 0);
-        if (count > 1) issue_item(1, 1);
+        if (nloc > 1) issue_item(1, 1);
     }
     // every wait is bounded, and the CTA decides together whether to go on
     // (__syncthreads_and), so no thread is left waiting at a barrier
     bool ok = __syncthreads_and(mbar_wait(&bars[2], 0));
     const uint32_t u = 2 * tid;  // this thread's two coefficients in the tile
-    for (uint32_t item = 0; item < count && ok; item++) {
-        const uint32_t b = item & 1;
-        ok = __syncthreads_and(mbar_wait(&bars[b], (item >> 1) & 1));
+    for (uint32_t k = 0; k < nloc && ok; k++) {
+        const uint32_t item = first + k, b = k & 1;
+        ok = __syncthreads_and(mbar_wait(&bars[b], (k >> 1) & 1));
         if (!ok) break;
         const uint64_t *buf = sbuf[b];
         U128 a0{0, 0}, a1{0, 0}, b0{0, 0}, b1{0, 0};
@@ -293,9 +302,9 @@ k_ip_bulk(const IpArgs A, const DevMod *__restrict__ mods, uint32_t log_n, uint3
         st2(y + (size_t(A.M) + i) * n, csub(redc(b0, m.q, m.qinv), m.q),
             csub(redc(b1, m.q, m.qinv), m.q));
         __syncthreads();  // everyone is done with buffer b
-        if (tid == 0 && item + 2 < count) {
+        if (tid == 0 && k + 2 < nloc) {
             fence_proxy_async();
-            issue_item(item + 2, b);
+            issue_item(k + 2, b);
         }
     }
     if (!ok && tid == 0) {
@@ -330,6 +339,37 @@ static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 static int launch_ip_regs(const Context &c, const IpArgs &a, uint32_t count, cudaStream_t s);
 
+// Ciphertext groups of a bulk inner-product launch: 1 to 4, whichever fills
+// the waves of CTAs best (resident CTAs per SM from the occupancy API), with
+// the groups' uneven sizes counted, and only if that beats one group by 10%
+// (each more group reloads its key tiles).  At N = 2^14 with 8 digits, 64
+// tiles x 9 limbs at 3 CTAs per SM is 1.26 waves in one group, 2.53 in two.
+template <typename K>
+static unsigned ip_groups(K kernel, unsigned threads, size_t smem, size_t ctas, uint32_t count) {
+    int dev = 0, sms = 0, occ = 0;
+    if (count < 2 || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, int(threads), smem) !=
+            cudaSuccess ||
+        sms <= 0 || occ <= 0)
+        return 1;
+    const double slots = double(sms) * occ;
+    auto score = [&](uint32_t g) {
+        const double waves = double(ctas) * g / slots;
+        const uint32_t per = (count + g - 1) / g;
+        return waves / std::ceil(waves) * (double(count) / g / per);
+    };
+    unsigned best = 1;
+    const double one = score(1);
+    double top = one;
+    for (uint32_t g = 2; g <= 4 && g <= count; g++)
+        if (score(g) > top + 1e-9) {
+            top = score(g);
+            best = g;
+        }
+    return top >= 1.1 * one ? best : 1;
+}
+
 int launch_ip(const Context &c, const IpArgs &a, uint32_t count, cudaStream_t s) {
     const size_t n = c.n;
     bool bulk = a.beta <= 8 && a.status != nullptr && n % 512 == 0 && aligned16(a.ext) &&
@@ -346,8 +386,9 @@ int launch_ip(const Context &c, const IpArgs &a, uint32_t count, cudaStream_t s)
         if (cudaFuncSetAttribute(k_ip_bulk<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                  int(smb)) != cudaSuccess)                                       \
             return CATFHE_ECUDA;                                                                 \
-        launch_pdl(k_ip_bulk<B>, dim3(unsigned(n / tile), a.M), dim3(tile / 2), smb, s, a,       \
-                   c.d_mods, c.log_n, count);                                                    \
+        const unsigned groups = ip_groups(k_ip_bulk<B>, tile / 2, smb, n / tile * a.M, count);   \
+        launch_pdl(k_ip_bulk<B>, dim3(unsigned(n / tile), a.M, groups), dim3(tile / 2), smb, s,  \
+                   a, c.d_mods, c.log_n, count);                                                 \
         break;                                                                                   \
     }
             IPB(1) IPB(2) IPB(3) IPB(4) IPB(5) IPB(6) IPB(7) IPB(8)
