@@ -31,6 +31,9 @@
 // KB) sits in shared memory and every thread reads the same words
 // (broadcast).
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include "launch.cuh"
 #include "modarith.cuh"
 
@@ -692,15 +695,31 @@ int launch_conv(const Context &c, const PlanList &plans, const uint64_t *src, si
 // thread on a tie, which spreads each CTA's plan copy over more work).  At
 // N = 2^14 with 24 rows and 4 resident CTAs per SM on 152 SMs, 4 per thread
 // (the fixed choice before) fills 63% of one wave; 3 per thread fills 87%.
+int resident_slots(const void *kernel, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, int, size_t>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    const auto key = std::make_tuple(dev, kernel, threads, smem);
+    {
+        std::lock_guard<std::mutex> g(mu);
+        const auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    int sms = 0, occ = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess ||
+        sms <= 0 || occ <= 0)
+        return 0;
+    std::lock_guard<std::mutex> g(mu);
+    return cache[key] = sms * occ;
+}
+
 template <typename K>
 static unsigned stride_columns(K kernel, size_t smem, size_t n, uint32_t items) {
-    int dev = 0, sms = 0, occ = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 256, smem) != cudaSuccess ||
-        sms <= 0 || occ <= 0)
-        return unsigned((n + 1023) / 1024);
-    const double slots = double(sms) * occ;
+    const int slots_i = resident_slots(reinterpret_cast<const void *>(kernel), 256, smem);
+    if (slots_i <= 0) return unsigned((n + 1023) / 1024);
+    const double slots = double(slots_i);
     double best = -1.0;
     unsigned cols = unsigned((n + 1023) / 1024);
     for (unsigned per = 1; per <= 8; per++) {

@@ -346,14 +346,10 @@ static int launch_ip_regs(const Context &c, const IpArgs &a, uint32_t count, cud
 // tiles x 9 limbs at 3 CTAs per SM is 1.26 waves in one group, 2.53 in two.
 template <typename K>
 static unsigned ip_groups(K kernel, unsigned threads, size_t smem, size_t ctas, uint32_t count) {
-    int dev = 0, sms = 0, occ = 0;
-    if (count < 2 || cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, int(threads), smem) !=
-            cudaSuccess ||
-        sms <= 0 || occ <= 0)
-        return 1;
-    const double slots = double(sms) * occ;
+    if (count < 2) return 1;
+    const int slots_i = resident_slots(reinterpret_cast<const void *>(kernel), int(threads), smem);
+    if (slots_i <= 0) return 1;
+    const double slots = double(slots_i);
     auto score = [&](uint32_t g) {
         const double waves = double(ctas) * g / slots;
         const uint32_t per = (count + g - 1) / g;

@@ -167,6 +167,9 @@ struct Keys {
 
 // Number of kernels this library has launched (all contexts, all threads).
 void note_launches(uint32_t k);
+// CTAs of `kernel` resident on the whole current device (SMs x CTAs per SM at
+// `threads` threads and `smem` dynamic shared bytes), 0 if unknown; cached.
+int resident_slots(const void *kernel, int threads, size_t smem);
 uint64_t launches_total();
 
 // ----------------------------------------------------------------- launchers
